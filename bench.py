@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the BinarySkyHough number count on one GB300 (or N, one process each).
+
+Metric: template-SFT terms per second (one term = one template x one SFT, the
+unit of the paper's stage-1 cost C1, Eq. (47)) over one pass of the whole hot
+path -- peakgram, weights, FP64 track tables, number count with the fused
+per-patch toplist, toplist merge, stage-2 power sum -- on the mid workload:
+2 detectors x 2000 SFTs (T_c = 900 s, 1 yr), 0.1 Hz at 200 Hz, 2000 sky points
+in 40 patches of 50, 32 a_p x 32 P x 32 t_asc, 90 f0 bins, top-1000 per patch,
+fp16 weights.  Synthetic, seeded inputs resident in HBM.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "template-SFT terms/sec and % of gather roofline, batched vs plain, on 1 GB300"
+UNIT = "terms/s"
+KERNELS_PER_STEP = 8   # peakgram, weights, 2 table kernels, count, merge, power, rerank
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mid", "small"], default="mid")
+    ap.add_argument("--graph", action="store_true", help="replay count+toplist+power as one CUDA graph")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_problem(kind: str, rank: int):
+    from paper_1904_04873_gb300 import synth
+    if kind == "mid":
+        sky = synth.fibonacci_sky(2000)
+    else:
+        sky = synth.fibonacci_sky(200)
+    if rank:
+        # each rank searches its own sky: the grid rotated about z by a rank-dependent angle
+        a = 2.399963 * rank
+        c, s = math.cos(a), math.sin(a)
+        sky = sky @ np.array([[c, s, 0.0], [-s, c, 0.0], [0.0, 0.0, 1.0]])
+    if kind == "mid":
+        return synth.mid(sky=sky)
+    return synth.mid(n_sky=200, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky)
+
+
+def workload_config(pr, kind):
+    return {"workload": f"{kind}: {pr.N} SFTs (2 det, T_c=900 s, 1 yr), band {pr.F0 / 900.0:.1f}-"
+                        f"{(pr.F0 + pr.n_f0) / 900.0:.1f} Hz, {pr.S} sky pts in patches of 50, "
+                        f"{pr.a_p.size}x{pr.Omega.size}x{pr.T_asc.shape[1]} binary, {pr.n_f0} f0, top-{pr.top_k}",
+            "templates": int(pr.n_templates), "terms_per_step": int(pr.n_terms), "weights": "fp16",
+            "l2": "256 MiB L2 flush write between steps"}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline_sample(pr, budget_s: float = 12.0):
+    """Time the FP64 oracle on whole templates of sky point 0 (all SFTs, all f0
+    bins, the first nb binary templates); returns (terms/s, sample text)."""
+    import oracle
+    rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
+    w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
+    op = oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky[:1],
+                              a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K)
+    t0 = time.perf_counter()
+    for b in range(2):
+        for j in range(pr.n_f0):
+            op.count_one(0, b, j)
+    dt = time.perf_counter() - t0
+    per_b = dt / 2
+    nb = max(2, min(pr.B, int(budget_s / max(per_b, 1e-6))))
+    t0 = time.perf_counter()
+    for b in range(nb):
+        for j in range(pr.n_f0):
+            op.count_one(0, b, j)
+    dt = time.perf_counter() - t0
+    terms = nb * pr.n_f0 * pr.N
+    return terms / dt, f"oracle count of sky point 0 x {nb} binary templates x {pr.n_f0} f0 x {pr.N} SFTs " \
+                       f"({terms:.3g} terms, {dt:.1f} s, single thread)"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pr = make_problem(args.workload, 0)
+    import oracle
+    rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
+    w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
+    op = oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky[:1],
+                              a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K)
+    nb = 16
+
+    def step(b0):
+        for b in range(b0, b0 + nb):
+            for j in range(pr.n_f0):
+                op.count_one(0, b % pr.B, j)
+
+    for k in range(args.warmup):
+        step(k * nb)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step((args.warmup + k) * nb)
+    dt = time.perf_counter() - t0
+    terms = args.steps * nb * pr.n_f0 * pr.N
+    v = terms / dt
+    sample = f"per step: oracle count of sky point 0 x {nb} binary templates x {pr.n_f0} f0 x {pr.N} SFTs"
+    print(json.dumps({"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "impl": "reference", "config": workload_config(pr, args.workload),
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_1904_04873_gb300 import build as _build
+    from paper_1904_04873_gb300 import bsh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    bsh.lib()
+
+    pr = make_problem(args.workload, rank)
+    stream = torch.cuda.current_stream()
+    dp = bsh.DeviceProblem(pr, w_dtype="f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=args.threads, sft_chunk=args.chunk)
+    n_cf = 100
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(k=None):
+        flush.fill_(k if k is not None else 0)
+        dp.prepare()
+        if k is not None:
+            ev[k][0].record(stream)
+        plan.number_count()
+        if k is not None:
+            ev[k][1].record(stream)
+        if args.graph:
+            plan.graph_launch(n_cf)
+        else:
+            plan.toplist()
+            plan.power_sum(n_cf)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    st = bsh.sync_status()
+    if st != bsh.OK:
+        raise SystemExit(f"device status {st} after warm-up")
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(k)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    count_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps
+    st = bsh.sync_status()
+    if st != bsh.OK:
+        raise SystemExit(f"device status {st} in timed region")
+
+    t_max = elapsed
+    terms_rank = pr.n_terms * args.steps
+    terms_all = terms_rank * world
+    if world > 1:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = terms_all / t_max
+
+    # ---- end to end through the public API: pinned host inputs -> device -> toplists -> host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
+                dict(power=pr.power, v=pr.v, t=pr.t, arms=pr.arms, Sn=pr.Sn, sky=pr.sky).items()}
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        out_host = torch.empty_like(plan.cands, device="cpu").pin_memory()
+        n_host = torch.empty_like(plan.n_cands, device="cpu").pin_memory()
+        fin_host = None
+
+        def e2e_step():
+            nonlocal fin_host
+            dp.power.copy_(host["power"], non_blocking=True)
+            dp.v.copy_(host["v"], non_blocking=True)
+            dp.t.copy_(host["t"], non_blocking=True)
+            dp.arms.copy_(host["arms"], non_blocking=True)
+            dp.Sn.copy_(host["Sn"], non_blocking=True)
+            dp.sky.copy_(host["sky"], non_blocking=True)
+            dp.prepare()
+            plan.number_count()
+            plan.toplist()
+            fin, nf = plan.power_sum(n_cf)
+            if fin_host is None:
+                fin_host = torch.empty_like(fin, device="cpu").pin_memory()
+            fin_host.copy_(fin, non_blocking=True)
+            n_host.copy_(nf, non_blocking=True)
+            return fin.numel() * fin.element_size() + nf.numel() * nf.element_size()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        ke = max(1, min(args.steps, 3))
+        a0.record(stream)
+        for _ in range(ke):
+            d2h = e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        te = a0.elapsed_time(a1) / 1e3
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": pr.n_terms * ke * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- plain form (FP64 track per term, FP64 weights, one launch per patch) on a bounded sample
+    plain = None
+    if not args.no_plain and rank == 0:
+        from paper_1904_04873_gb300 import synth
+        sub = synth.mid(sky=pr.sky[:4], patch_size=50) if args.workload == "mid" else \
+            synth.mid(n_sky=4, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=pr.sky[:4])
+        dps = bsh.DeviceProblem(sub, w_dtype="f64")
+        dps.prepare()
+        pplan = bsh.Plan([dps], bsh.MODE_PLAIN, top_k=pr.top_k)
+        pplan.number_count()
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        pplan.number_count()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        tp = b0.elapsed_time(b1) / 1e3
+        plain = {"value": sub.n_terms / tp, "unit": UNIT, "sample": f"plain form on {sub.S} sky points x "
+                 f"{sub.B} binaries x {sub.n_f0} f0 x {sub.N} SFTs (one launch per patch)", "ms": tp * 1e3}
+        pplan.close()
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    count_rate = pr.n_terms / count_s
+    achieved_gbs = count_rate * 4.0 / 1e9
+    peak_gbs = n_sm * 128.0 * f_max / 1e9
+    roofline = {"bound": "smem", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved_gbs / peak_gbs, "traffic": None,
+                "kernel": "bsh_number_count (track tables + count_batched)",
+                "peak_source": f"derived: {n_sm} SMs x 32 banks x 4 B/clk x {f_max / 1e6:.0f} MHz "
+                               f"(MEASURED_PEAKS sm_max_mhz); one 32-bit word per term",
+                "terms_per_s": count_rate, "count_ms": count_s * 1e3}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        v, sample = cpu_baseline_sample(pr)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
+                "config": workload_config(pr, args.workload) | {"parallelism": f"replicas x{world}",
+                                                                  "graph": bool(args.graph)},
+                "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline,
+                "plain": plain, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

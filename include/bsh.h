@@ -1,0 +1,255 @@
+/*
+ * bsh.h -- C ABI of the GB300-native BinarySkyHough number count.
+ *
+ * Method: P. B. Covas and A. M. Sintes, "BinarySkyHough: a new method to
+ * search for continuous gravitational waves from unknown neutron stars in
+ * binary systems", arXiv:1904.04873.  Section / equation numbers below are
+ * the paper's.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller unless the
+ *     comment says HOST.  The library never allocates device memory: the
+ *     only device memory it uses besides the caller's arrays is the plan
+ *     workspace the caller passes to bsh_plan_bind().
+ *   - Calls taking a stream only enqueue work on it (asynchronous).  Those
+ *     marked "capturable" make no host synchronisation and no allocation and
+ *     may be recorded into a CUDA graph.
+ *   - Every call returns BSH_OK or one of the BSH_ERR_* codes below.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *     Errors found by kernels (a track leaving the loaded band, a fixed-point
+ *     table out of range, a bounded wait that expired) are recorded in a
+ *     device status word and returned by bsh_sync_status().  No kernel traps
+ *     or prints.
+ *   - Row-major layouts: [a][b] means b is the fastest index.
+ *   - Frequencies are bin numbers F = f * T_c (Eq. (33): delta f = 1/T_c).
+ *   - Template order inside a problem: id = ((s * B + b) * n_f0 + j) with the
+ *     binary index b = (iOm * n_T + iT) * n_ap + iap and F_j = F0 + j.
+ */
+#ifndef BSH_H
+#define BSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (NULL = legacy default stream). */
+typedef struct CUstream_st* bsh_stream;
+
+enum {
+    BSH_OK = 0,
+    BSH_ERR_ARG = 1,        /* bad shape, null pointer, misalignment, unsupported option */
+    BSH_ERR_RANGE = 2,      /* a track leaves [k_lo, k_lo + K) or a parameter is outside the fixed-point range */
+    BSH_ERR_TIMEOUT = 3,    /* a bounded device wait expired */
+    BSH_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    BSH_ERR_WORKSPACE = 5,  /* workspace missing or too small */
+    BSH_ERR_STATE = 6       /* call order violated (e.g. plan not bound) */
+};
+
+/* Weight / accumulation dtypes. */
+enum { BSH_F64 = 0, BSH_F32 = 1, BSH_F16 = 2, BSH_BF16 = 3 };
+
+/* Number-count modes. */
+enum {
+    BSH_MODE_BATCHED = 0,   /* one persistent launch over every problem and patch, fixed-point
+                               track with exact FP64 fallback, FP32 Kahan-compensated sums */
+    BSH_MODE_PLAIN = 1      /* one launch per sky patch, FP64 track for every term, FP64 sums */
+};
+
+/* Text for a status code (static storage). */
+const char* bsh_error_string(int status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int bsh_version(void);
+
+/*
+ * Reads the device status word written by kernels of this library on the
+ * current device, clears it and returns it as a BSH_* code (BSH_OK when no
+ * kernel reported an error).  Synchronises `stream`.  Not capturable.
+ */
+int bsh_sync_status(bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* (i) Peakgram, Sec. IV.A, Eq. (20)-(21).                                   */
+/*                                                                          */
+/* power [N][K] float: SFT powers |x~|^2 of the loaded band (or, with        */
+/*   median_window = 0, normalised powers rho given directly).               */
+/* median_window: odd width of the running median (the paper uses 101), or   */
+/*   0.  The noise floor is <n>^2 = median / ln 2 (median of Exp(1) is ln 2); */
+/*   near the band edges the window is shifted, not truncated, so K must be   */
+/*   >= median_window.                                                        */
+/* rho_out [N][K] float (may be NULL): rho = P ln2 / median, rounded once    */
+/*   from double.                                                             */
+/* bits [N][W] uint32: bit (k & 31) of word k/32 of row i is 1 when          */
+/*   P ln2 > rho_th * median (both products rounded in double), i.e.          */
+/*   rho > rho_th.  W >= ceil(K/32); the padding bits are written as 0.       */
+/* Capturable.                                                               */
+/* ------------------------------------------------------------------------ */
+int bsh_make_peakgram(const float* power, int N, int K, int median_window, double rho_th,
+                      float* rho_out, uint32_t* bits, int W, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* (ii) Weights, Sec. IV.A, Eq. (22): w_i(n) = (F+^2 + Fx^2)/S_n,i at the     */
+/* SFT mid-time, with F+, Fx the antenna patterns of Eq. (1).                */
+/*                                                                          */
+/* sky [S][3] double: unit propagation-source directions (equatorial).       */
+/* arms [N][6] double: unit vectors of the x arm then the y arm of the        */
+/*   detector that took SFT i, at its mid-time, same frame.                   */
+/* Sn [N] double: noise level S_n of SFT i in the band (> 0).                */
+/* normalize: 1 scales each sky point's weights to sum to N; 0 leaves them.  */
+/* dtype: BSH_F64 / F32 / F16 / BF16, the stored type of w (round to nearest */
+/*   even from the double value).                                            */
+/* w [S][N] of dtype.  sum_w, sum_w2 [S] double (may be NULL): sums of the   */
+/*   stored (quantised) weights and of their squares, for Eq. (25).          */
+/* A sky point whose weights sum to zero records BSH_ERR_RANGE.  Capturable. */
+/* ------------------------------------------------------------------------ */
+int bsh_weights(const double* sky, int S, const double* arms, const double* Sn, int N,
+                int normalize, int dtype, void* w, double* sum_w, double* sum_w2,
+                bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Search problem: one loaded frequency band, a sky set split into patches   */
+/* and a circular-orbit binary grid (Sec. V.A-V.B).                           */
+/* ------------------------------------------------------------------------ */
+typedef struct bsh_problem {
+    /* band */
+    int N;                     /* SFTs, all detectors concatenated (option B) */
+    int k_lo;                  /* bin number of column 0 of the loaded band */
+    int K;                     /* loaded bins per SFT */
+    int W;                     /* words per peakgram row, >= ceil(K/32), multiple of 4 */
+    const uint32_t* bits;      /* [N][W] peakgram from bsh_make_peakgram, 16-byte aligned */
+    const float* rho;          /* [N][K] rho for stage 2, or NULL if bsh_power_sum is not used */
+    const void* w;             /* [S][N] weights of w_dtype */
+    int w_dtype;               /* BSH_F64 / F32 / F16 / BF16 */
+    const double* sum_w;       /* [S] sum of w over SFTs */
+    const double* sum_w2;      /* [S] sum of w^2 over SFTs */
+    const double* v;           /* [N][3] detector velocity / c at the SFT mid-time */
+    const double* t;           /* [N] SFT mid-time (s) relative to the reference time */
+    double v_max;              /* bound on |v_i| (checked on the device) */
+    /* frequency templates: F_j = F0 + j, j < n_f0; F0 integer or half-integer */
+    double F0;
+    int n_f0;
+    /* sky */
+    int S;
+    const double* sky;         /* [S][3] unit vectors */
+    int n_patch;
+    const int64_t* patch_start;/* HOST [n_patch + 1]: patch p = sky points [start[p], start[p+1]) */
+    /* binary grid, HOST arrays (copied by bsh_plan_create) */
+    int n_ap;
+    const double* a_p;         /* [n_ap] projected semi-major axis (light-seconds), >= 0 */
+    int n_Om;
+    const double* Omega;       /* [n_Om] orbital angular frequency 2 pi / P (rad/s), > 0 */
+    int n_T;
+    const double* T_asc;       /* [n_Om][n_T] time of ascension (s), Eq. (35) range */
+    double rho_th;             /* peak threshold used for the peakgram (1.6), Eq. (25) mean */
+} bsh_problem;
+
+typedef struct bsh_count_options {
+    int mode;                  /* BSH_MODE_BATCHED or BSH_MODE_PLAIN */
+    int top_k;                 /* toplist length per patch (N_C of Sec. IV.C), 1..16384 */
+    int threads;               /* CTA size: 0 = autotuned / default, else 128 or 256 */
+    int sft_chunk;             /* SFTs per shared-memory stage: 0 = default, else 64, 128 or 256 */
+    int ctas_per_sm;           /* 0 = default */
+} bsh_count_options;
+
+typedef struct bsh_plan bsh_plan;
+
+/* Validates the problems on the host, picks the fixed-point scales and the
+ * static persistent schedule.  HOST only, no CUDA call.  patch_start and the
+ * grid arrays are copied; device pointers are stored and used by later calls.
+ * Returns BSH_ERR_RANGE when the band does not cover every track, when a
+ * parameter leaves the fixed-point range, or when a patch holds 2^32 or more
+ * templates. */
+int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count_options* opt,
+                    bsh_plan** plan);
+void bsh_plan_destroy(bsh_plan* plan);
+
+/* Device workspace bytes the plan needs (tables, schedule, toplist buffers). */
+size_t bsh_plan_workspace_size(const bsh_plan* plan);
+
+/* Number of toplist regions (sum of n_patch over the problems); region r of
+ * problem q is q's patch (r - first_region(q)). */
+int bsh_plan_num_regions(const bsh_plan* plan);
+int bsh_plan_first_region(const bsh_plan* plan, int problem);
+
+/* Attaches the caller's workspace (256-byte aligned device memory of at least
+ * bsh_plan_workspace_size bytes) and uploads the plan's small tables with
+ * stream-ordered copies; synchronises `stream`.  Not capturable; call once. */
+int bsh_plan_bind(bsh_plan* plan, void* workspace, size_t bytes, bsh_stream stream);
+
+/* Runs the autotuner: times the candidate tile shapes on a slice of the work
+ * list and keeps the fastest.  Synchronises; not capturable. */
+int bsh_autotune(bsh_plan* plan, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */
+/* sum n = sum_i w_i * bit_i[k_i] along the track k_i = round(f(t_i) T_c) of  */
+/* Eq. (15), its significance s_H of Eq. (25), and a fused per-patch         */
+/* toplist of the top_k largest s_H (ties: smaller template id first).       */
+/* Reads the problems' bits, w, sums, v, t and sky arrays.  Capturable.      */
+/* ------------------------------------------------------------------------ */
+int bsh_number_count(bsh_plan* plan, bsh_stream stream);
+
+/* Debug / parity form of (iii): writes every template's counts instead of a
+ * toplist.  n_unw[q] and n_w[q] are HOST arrays of n_problems DEVICE pointers
+ * to [S][B][n_f0] int32 / float buffers.  Capturable. */
+int bsh_count_dense(bsh_plan* plan, int32_t* const* n_unw, float* const* n_w, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* (iv) Toplist, Sec. IV.C: merges the per-CTA candidate lists of each        */
+/* region into its top_k templates, sorted by s_H (descending, ties by       */
+/* template id).                                                              */
+/* out [regions][top_k]; n_out [regions] entries written.  Capturable.       */
+/* ------------------------------------------------------------------------ */
+typedef struct bsh_cand {
+    int64_t template_id;       /* ((s * B + b) * n_f0 + j) within the problem */
+    float s_h;                 /* Eq. (25) */
+    float n_w;                 /* weighted number count */
+    int32_t n_unw;             /* unweighted number count */
+    float power;               /* Eq. (26) P, set by bsh_power_sum */
+    float s_p;                 /* Eq. (26) s_P, set by bsh_power_sum */
+    int32_t region;            /* toplist region (problem's first region + patch) */
+} bsh_cand;
+
+int bsh_toplist(bsh_plan* plan, bsh_cand* out, int32_t* n_out, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* (v) Stage 2, Sec. IV.C, Eq. (26): for every candidate the summed weighted  */
+/* normalised power P = sum_i w_i rho_i[k_i] along the exact track, and       */
+/* s_P = (P - sum w)/sqrt(sum w^2); then each region's list is re-ranked by  */
+/* s_P (descending, ties by template id) and cut to n_cf (N_CF).             */
+/* cands [regions][top_k] and n_cands [regions] as written by bsh_toplist     */
+/* (power and s_p are filled in place); final [regions][n_cf], n_final       */
+/* [regions].  Needs every problem's rho.  Capturable.                        */
+/* ------------------------------------------------------------------------ */
+int bsh_power_sum(bsh_plan* plan, bsh_cand* cands, const int32_t* n_cands, int n_cf,
+                  bsh_cand* final_list, int32_t* n_final, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* CUDA-graph form of (iii)+(iv)+(v): the first call records the three calls */
+/* on `stream` into a graph owned by the plan, later calls replay it.         */
+/* Arguments as for bsh_toplist and bsh_power_sum; changing them requires     */
+/* bsh_graph_reset.  Not capturable itself.                                   */
+/* ------------------------------------------------------------------------ */
+int bsh_graph_launch(bsh_plan* plan, bsh_cand* cands, int32_t* n_cands, int n_cf,
+                     bsh_cand* final_list, int32_t* n_final, bsh_stream stream);
+int bsh_graph_reset(bsh_plan* plan);
+
+/* ------------------------------------------------------------------------ */
+/* Host-side checks of the fixed-point track (no GPU needed).                 */
+/* Evaluates, on the host with the same code as the kernels, the 32-bit       */
+/* peak window of templates (s, b, block j0..j0+31) at SFT i for `count`      */
+/* queries: row_bits [count][W] holds the row of each query; out [count]     */
+/* receives the windows and path [count] the path taken (0 fast, 1 crossing,  */
+/* 2 exact-fallback).  Inputs as in bsh_problem but HOST arrays.  Used by the */
+/* CPU tests against the oracle.                                              */
+/* ------------------------------------------------------------------------ */
+int bsh_debug_track_windows(const bsh_problem* host_problem, const int32_t* query /*[count][4]: s,b,i,j0*/,
+                            int count, const uint32_t* row_bits, uint32_t* out, int32_t* path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSH_H */

@@ -1,0 +1,327 @@
+"""Thin ctypes binding to libbsh (include/bsh.h): argument marshalling only.
+
+Device memory comes from PyTorch tensors; every step of the hot path runs in
+the library's CUDA kernels.  Loading fails loudly when the library has not
+been built (``python -m paper_1904_04873_gb300.build`` or
+``__graft_entry__.build()``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbsh.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_RANGE, ERR_TIMEOUT, ERR_CUDA, ERR_WORKSPACE, ERR_STATE = range(7)
+F64, F32, F16, BF16 = range(4)
+MODE_BATCHED, MODE_PLAIN = 0, 1
+DTYPE_CODES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+
+
+class BshError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().bsh_error_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int), ("k_lo", ctypes.c_int), ("K", ctypes.c_int), ("W", ctypes.c_int),
+        ("bits", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("w", ctypes.c_void_p),
+        ("w_dtype", ctypes.c_int),
+        ("sum_w", ctypes.c_void_p), ("sum_w2", ctypes.c_void_p), ("v", ctypes.c_void_p),
+        ("t", ctypes.c_void_p), ("v_max", ctypes.c_double), ("F0", ctypes.c_double),
+        ("n_f0", ctypes.c_int), ("S", ctypes.c_int), ("sky", ctypes.c_void_p),
+        ("n_patch", ctypes.c_int), ("patch_start", ctypes.c_void_p),
+        ("n_ap", ctypes.c_int), ("a_p", ctypes.c_void_p),
+        ("n_Om", ctypes.c_int), ("Omega", ctypes.c_void_p),
+        ("n_T", ctypes.c_int), ("T_asc", ctypes.c_void_p),
+        ("rho_th", ctypes.c_double),
+    ]
+
+
+class CountOptions(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("top_k", ctypes.c_int), ("threads", ctypes.c_int),
+                ("sft_chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class Cand(ctypes.Structure):
+    _fields_ = [("template_id", ctypes.c_int64), ("s_h", ctypes.c_float), ("n_w", ctypes.c_float),
+                ("n_unw", ctypes.c_int32), ("power", ctypes.c_float), ("s_p", ctypes.c_float),
+                ("region", ctypes.c_int32)]
+
+
+CAND_DTYPE = np.dtype([("template_id", "<i8"), ("s_h", "<f4"), ("n_w", "<f4"), ("n_unw", "<i4"),
+                       ("power", "<f4"), ("s_p", "<f4"), ("region", "<i4")])
+assert CAND_DTYPE.itemsize == ctypes.sizeof(Cand) == 32
+
+_SIGS = {
+    "bsh_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "bsh_version": (ctypes.c_int, []),
+    "bsh_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_make_peakgram": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "bsh_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "bsh_plan_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(CountOptions),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "bsh_plan_destroy": (None, [ctypes.c_void_p]),
+    "bsh_plan_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "bsh_plan_num_regions": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_plan_first_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bsh_plan_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "bsh_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_number_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_count_dense": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_toplist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_power_sum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_graph_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libbsh.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libbsh.so not built ({LIB_PATH}); run paper_1904_04873_gb300/build.py")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise BshError(rc, where)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def sync_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status code."""
+    return lib().bsh_sync_status(_stream(stream))
+
+
+# ------------------------------------------------------------ (i) peakgram
+
+def make_peakgram(power, median_window: int, rho_th: float = 1.6, W: Optional[int] = None,
+                  want_rho: bool = True, out_bits=None, out_rho=None, stream=None):
+    import torch
+    assert power.is_cuda and power.dtype == torch.float32 and power.is_contiguous()
+    N, K = power.shape
+    if W is None:
+        W = -(-K // 32)
+        W = -(-W // 4) * 4
+    bits = out_bits if out_bits is not None else torch.empty((N, W), dtype=torch.int32, device=power.device)
+    rho = None
+    if want_rho:
+        rho = out_rho if out_rho is not None else torch.empty((N, K), dtype=torch.float32, device=power.device)
+    _check(lib().bsh_make_peakgram(_ptr(power), N, K, median_window, float(rho_th), _ptr(rho), _ptr(bits), W,
+                                   _stream(stream)), "bsh_make_peakgram")
+    return rho, bits
+
+
+# ------------------------------------------------------------- (ii) weights
+
+def weights(sky, arms, Sn, normalize: bool = True, dtype: str = "f16", out=None, stream=None):
+    import torch
+    tdt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    S, N = sky.shape[0], Sn.shape[0]
+    if out is None:
+        w = torch.empty((S, N), dtype=tdt, device=sky.device)
+        sw = torch.empty(S, dtype=torch.float64, device=sky.device)
+        sw2 = torch.empty(S, dtype=torch.float64, device=sky.device)
+    else:
+        w, sw, sw2 = out
+    _check(lib().bsh_weights(_ptr(sky), S, _ptr(arms), _ptr(Sn), N, int(normalize), DTYPE_CODES[dtype], _ptr(w),
+                             _ptr(sw), _ptr(sw2), _stream(stream)), "bsh_weights")
+    return w, sw, sw2
+
+
+# -------------------------------------------------------- problems and plans
+
+class DeviceProblem:
+    """A synth.Problem resident on the GPU, with its peakgram and weights buffers."""
+
+    def __init__(self, pr, device="cuda", w_dtype: str = "f16"):
+        import torch
+        self.pr = pr
+        self.device = device
+        f64 = dict(dtype=torch.float64, device=device)
+        self.t = torch.as_tensor(pr.t, **f64)
+        self.v = torch.as_tensor(pr.v, **f64).contiguous()
+        self.arms = torch.as_tensor(pr.arms, **f64).contiguous()
+        self.Sn = torch.as_tensor(pr.Sn, **f64)
+        self.sky = torch.as_tensor(pr.sky, **f64).contiguous()
+        self.power = torch.as_tensor(pr.power, dtype=torch.float32, device=device).contiguous()
+        self.w_dtype = w_dtype
+        self.v_max = float(np.max(np.linalg.norm(pr.v, axis=1))) * (1.0 + 1e-9)
+        N, K, W, S = pr.N, pr.K, pr.W, pr.S
+        self.bits = torch.empty((N, W), dtype=torch.int32, device=device)
+        self.rho = torch.empty((N, K), dtype=torch.float32, device=device)
+        tdt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[w_dtype]
+        self.w = torch.empty((S, N), dtype=tdt, device=device)
+        self.sum_w = torch.empty(S, **f64)
+        self.sum_w2 = torch.empty(S, **f64)
+
+    def prepare(self, stream=None):
+        """Rows (i) and (ii): peakgram and weights from the resident inputs."""
+        pr = self.pr
+        make_peakgram(self.power, pr.median_window, pr.rho_th, pr.W, out_bits=self.bits, out_rho=self.rho,
+                      stream=stream)
+        weights(self.sky, self.arms, self.Sn, True, self.w_dtype, out=(self.w, self.sum_w, self.sum_w2),
+                stream=stream)
+
+    def descriptor(self) -> Problem:
+        pr = self.pr
+        self._ps = np.ascontiguousarray(pr.patch_start, dtype=np.int64)
+        self._ap = np.ascontiguousarray(pr.a_p, dtype=np.float64)
+        self._Om = np.ascontiguousarray(pr.Omega, dtype=np.float64)
+        self._Ta = np.ascontiguousarray(pr.T_asc, dtype=np.float64)
+        return Problem(N=pr.N, k_lo=pr.k_lo, K=pr.K, W=pr.W, bits=_ptr(self.bits), rho=_ptr(self.rho),
+                       w=_ptr(self.w), w_dtype=DTYPE_CODES[self.w_dtype], sum_w=_ptr(self.sum_w),
+                       sum_w2=_ptr(self.sum_w2), v=_ptr(self.v), t=_ptr(self.t), v_max=self.v_max,
+                       F0=float(pr.F0), n_f0=pr.n_f0, S=pr.S, sky=_ptr(self.sky),
+                       n_patch=len(self._ps) - 1, patch_start=self._ps.ctypes.data,
+                       n_ap=self._ap.size, a_p=self._ap.ctypes.data, n_Om=self._Om.size,
+                       Omega=self._Om.ctypes.data, n_T=self._Ta.shape[1], T_asc=self._Ta.ctypes.data,
+                       rho_th=float(pr.rho_th))
+
+
+class Plan:
+    """bsh_plan with its workspace (a torch uint8 tensor) and output buffers."""
+
+    def __init__(self, problems: Sequence[DeviceProblem], mode: int = MODE_BATCHED, top_k: int = 1000,
+                 threads: int = 0, sft_chunk: int = 0, ctas_per_sm: int = 0, stream=None):
+        import torch
+        self.problems = list(problems)
+        descs = (Problem * len(self.problems))(*[p.descriptor() for p in self.problems])
+        self._descs = descs
+        opt = CountOptions(mode=mode, top_k=top_k, threads=threads, sft_chunk=sft_chunk, ctas_per_sm=ctas_per_sm)
+        h = ctypes.c_void_p()
+        _check(lib().bsh_plan_create(descs, len(self.problems), ctypes.byref(opt), ctypes.byref(h)),
+               "bsh_plan_create")
+        self.h = h
+        self.top_k = top_k
+        self.mode = mode
+        dev = self.problems[0].device
+        self.ws_bytes = lib().bsh_plan_workspace_size(h)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        _check(lib().bsh_plan_bind(h, ctypes.c_void_p(self._ws_ptr), self.ws_bytes, _stream(stream)), "bsh_plan_bind")
+        self.regions = lib().bsh_plan_num_regions(h)
+        self.cands = torch.zeros((self.regions, top_k, 32), dtype=torch.uint8, device=dev)
+        self.n_cands = torch.zeros(self.regions, dtype=torch.int32, device=dev)
+        self.final = None
+        self.n_final = None
+
+    def first_region(self, q: int) -> int:
+        return lib().bsh_plan_first_region(self.h, q)
+
+    def number_count(self, stream=None):
+        _check(lib().bsh_number_count(self.h, _stream(stream)), "bsh_number_count")
+
+    def count_dense(self, stream=None):
+        import torch
+        outs_u, outs_w = [], []
+        for p in self.problems:
+            pr = p.pr
+            outs_u.append(torch.full((pr.S, pr.B, pr.n_f0), -1, dtype=torch.int32, device=p.device))
+            outs_w.append(torch.full((pr.S, pr.B, pr.n_f0), float("nan"), dtype=torch.float32, device=p.device))
+        pu = (ctypes.c_void_p * len(outs_u))(*[o.data_ptr() for o in outs_u])
+        pw = (ctypes.c_void_p * len(outs_w))(*[o.data_ptr() for o in outs_w])
+        _check(lib().bsh_count_dense(self.h, pu, pw, _stream(stream)), "bsh_count_dense")
+        return outs_u, outs_w
+
+    def toplist(self, stream=None):
+        _check(lib().bsh_toplist(self.h, _ptr(self.cands), _ptr(self.n_cands), _stream(stream)), "bsh_toplist")
+        return self.cands, self.n_cands
+
+    def _final_buffers(self, n_cf):
+        import torch
+        if self.final is None or self.final.shape[1] != n_cf:
+            dev = self.problems[0].device
+            self.final = torch.zeros((self.regions, n_cf, 32), dtype=torch.uint8, device=dev)
+            self.n_final = torch.zeros(self.regions, dtype=torch.int32, device=dev)
+
+    def power_sum(self, n_cf: int, stream=None):
+        self._final_buffers(n_cf)
+        _check(lib().bsh_power_sum(self.h, _ptr(self.cands), _ptr(self.n_cands), n_cf, _ptr(self.final),
+                                   _ptr(self.n_final), _stream(stream)), "bsh_power_sum")
+        return self.final, self.n_final
+
+    def graph_launch(self, n_cf: int, stream=None):
+        self._final_buffers(n_cf)
+        _check(lib().bsh_graph_launch(self.h, _ptr(self.cands), _ptr(self.n_cands), n_cf, _ptr(self.final),
+                                      _ptr(self.n_final), _stream(stream)), "bsh_graph_launch")
+        return self.final, self.n_final
+
+    def autotune(self, stream=None):
+        _check(lib().bsh_autotune(self.h, _stream(stream)), "bsh_autotune")
+
+    def close(self):
+        if self.h:
+            lib().bsh_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cands_to_numpy(cands, n) -> List[np.ndarray]:
+    """Device toplists -> one structured numpy array per region."""
+    raw = cands.cpu().numpy()
+    nn = n.cpu().numpy()
+    return [raw[r, :nn[r]].copy().view(CAND_DTYPE).reshape(-1) for r in range(raw.shape[0])]
+
+
+def debug_track_windows(pr, queries: np.ndarray, rows: np.ndarray):
+    """Host evaluation of the kernels' fixed-point windows (no GPU needed)."""
+    q = np.ascontiguousarray(queries, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    n = q.shape[0]
+    out = np.zeros(n, np.uint32)
+    path = np.zeros(n, np.int32)
+    arrs = dict(v=np.ascontiguousarray(pr.v), t=np.ascontiguousarray(pr.t), sky=np.ascontiguousarray(pr.sky),
+                ap=np.ascontiguousarray(pr.a_p), Om=np.ascontiguousarray(pr.Omega),
+                Ta=np.ascontiguousarray(pr.T_asc))
+    v_max = float(np.max(np.linalg.norm(pr.v, axis=1))) * (1.0 + 1e-9)
+    d = Problem(N=pr.N, k_lo=pr.k_lo, K=pr.K, W=pr.W, v=arrs["v"].ctypes.data, t=arrs["t"].ctypes.data,
+                v_max=v_max, F0=float(pr.F0), n_f0=pr.n_f0, S=pr.S, sky=arrs["sky"].ctypes.data, n_patch=1,
+                n_ap=arrs["ap"].size, a_p=arrs["ap"].ctypes.data, n_Om=arrs["Om"].size,
+                Omega=arrs["Om"].ctypes.data, n_T=arrs["Ta"].shape[1], T_asc=arrs["Ta"].ctypes.data,
+                rho_th=float(pr.rho_th))
+    _check(lib().bsh_debug_track_windows(ctypes.byref(d), q.ctypes.data, n, rows.ctypes.data, out.ctypes.data,
+                                         path.ctypes.data), "bsh_debug_track_windows")
+    return out, path

@@ -1,0 +1,312 @@
+// Internal declarations shared by the CUDA translation units of libbsh.
+//
+// Track arithmetic (Eq. (15) times T_c):
+//   k_i(j) = floor(F_j + F_j * D_i + 1/2),  D_i = v_i.n - a_p * Omega * cos(Omega (t_i - t_asc))
+// The hot kernels evaluate it in 32-bit fixed point, with a rigorous error
+// bound eps, and fall back to the exact FP64 expression whenever the fixed-point
+// value lies within M > eps of a rounding boundary.  The fixed-point value of
+//   v(j) = F_j * D + frac(F_j) + 1/2        (units of bins, scale 2^s_y)
+// is Z(j) - mulhi(ap_q, C_q(j)) with
+//   Z(j)   = round(F_j * vn * 2^s_y) + (frac(F_j) + 1/2) 2^s_y    from vn_q = round(vn 2^s_vn)
+//   C_q(j) = round(F_j * c * 2^s_C)                               from c_q  = round(c 2^s_c), c = Omega cos(..)
+//   ap_q   = round(a_p 2^s_a),  s_y = s_a + s_C - 32
+// and the bin is floor(F_j) + floor(v(j) / 2^s_y).  Since v is linear in j, a
+// block of 32 consecutive f0 templates needs v only at j0 and j0 + 31.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bsh.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace bsh {
+
+constexpr int MAX_PROBLEMS = 8;
+constexpr int JW = 32;            // f0 templates per thread (one 32-bit peak window)
+
+// Device status word bits (reported as the lowest set code by bsh_sync_status).
+enum : unsigned {
+    ST_RANGE = 1u << 0,
+    ST_TIMEOUT = 1u << 1,
+    ST_ARG = 1u << 2,
+};
+
+__device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
+#ifdef __CUDA_ARCH__
+    atomicOr(status, bit);
+#else
+    *status |= bit;
+#endif
+}
+
+// Fixed-point parameters of one problem (chosen on the host, see plan.cu).
+struct FixedPoint {
+    int s_vn, s_c, s_a, s_C, s_y;
+    int sh_v, sh_c;               // right shifts producing Z and C_q from the tables
+    int M;                        // decision margin (units of 2^-s_y bins)
+    int off_q;                    // (frac(F0) + 1/2) 2^s_y
+    double eps;                   // error bound of v (units of 2^-s_y bins)
+};
+
+// Per-problem data seen by the kernels.
+struct ProbDev {
+    // caller arrays
+    const uint32_t* bits;     // [N][W]
+    const float* rho;         // [N][K]
+    const void* w;            // [S][N] (w_dtype)
+    const double* sum_w;      // [S]
+    const double* sum_w2;     // [S]
+    const double* v;          // [N][3]
+    const double* t;          // [N]
+    const double* sky;        // [S][3]
+    // workspace tables
+    int32_t* vn_q;            // [S][Np]
+    int32_t* c_q;             // [nOT][Np]
+    double* c64;              // [nOT][Np]
+    float* w32;               // [S][Np]   (batched mode)
+    double* w64;              // [S][Np]   (plain mode)
+    const double* a_p;        // [n_ap]
+    const int32_t* ap_q;      // [n_ap]
+    const double* Om;         // [n_Om]
+    const double* Tasc;       // [n_Om * n_T]
+    const int64_t* patch_start;  // [n_patch + 1]
+    const int32_t* patch_of_s;   // [S]
+    // sizes
+    int N, Np, K, W, k_lo, n_f0, S, n_ap, n_Om, n_T, nOT, B, n_patch, w_dtype;
+    double F0;                // first template (bins)
+    int G0;                   // floor(F0)
+    int JB;                   // valid templates per f0 block (<= 32)
+    int n_fb, n_bt;           // f0 blocks, binary tiles
+    int ot_tile;              // Omega-T rows staged per binary tile
+    FixedPoint fp;
+    int o_min, o_max;         // bounds of floor(v / 2^s_y)
+    int Wseg;                 // staged words per row
+    double p_th;              // exp(-rho_th)
+    double v_max;
+    int region_base;
+    int64_t item_begin, n_items;
+    int64_t cost;             // cost units per item
+};
+
+// Entry of a toplist buffer: key = (order-preserving bits of s_H) << 32 | (2^32 - 1 - local id).
+struct Entry {
+    unsigned long long key;
+    float n_w;
+    int32_t n_unw;
+};
+static_assert(sizeof(Entry) == 16, "Entry layout");
+
+__host__ __device__ __forceinline__ uint32_t float_order(float f) {
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    union { float f; uint32_t u; } cv;
+    cv.f = f;
+    u = cv.u;
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float order_float(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    union { float f; uint32_t u; } cv;
+    cv.u = u;
+    return cv.f;
+#endif
+}
+
+__host__ __device__ __forceinline__ unsigned long long make_key(float score, uint32_t lid) {
+    return ((unsigned long long)float_order(score) << 32) | (unsigned long long)(0xffffffffu - lid);
+}
+
+__host__ __device__ __forceinline__ int mulhi32(int a, int b) {
+#ifdef __CUDA_ARCH__
+    return __mulhi(a, b);
+#else
+    return (int)(((long long)a * (long long)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
+
+// Z(j) from a vn table entry: round(F2 * vn_q / 2^sh_v) + off_q, F2 = 2 F_j.
+__host__ __device__ __forceinline__ int make_Z(int F2, int vn_q, const FixedPoint& fp) {
+    long long p = (long long)F2 * (long long)vn_q;
+    long long r = fp.sh_v > 0 ? ((p + (1LL << (fp.sh_v - 1))) >> fp.sh_v) : p;
+    return (int)r + fp.off_q;
+}
+
+// C_q(j) from a c table entry: round(F2 * c_q / 2^sh_c).
+__host__ __device__ __forceinline__ int make_C(int F2, int c_q, const FixedPoint& fp) {
+    long long p = (long long)F2 * (long long)c_q;
+    long long r = fp.sh_c > 0 ? ((p + (1LL << (fp.sh_c - 1))) >> fp.sh_c) : p;
+    return (int)r;
+}
+
+// Fast path: both ends of the block, widened by M, fall in the same bin cell.
+__host__ __device__ __forceinline__ bool fp_fast(int v0, int v1, int s_y, int M) {
+    int lo = imin(v0, v1) - M;
+    int hi = imax(v0, v1) + M;
+    return ((unsigned)(lo ^ hi) >> s_y) == 0u;
+}
+
+// 32 consecutive bits of a staged row starting at bit position pos (0 <= pos <= 32*Wseg - 33).
+__host__ __device__ __forceinline__ uint32_t row_window(const uint32_t* row, int pos) {
+    uint32_t w0 = row[pos >> 5], w1 = row[(pos >> 5) + 1];
+#ifdef __CUDA_ARCH__
+    return __funnelshift_r(w0, w1, pos & 31);
+#else
+    int sh = pos & 31;
+    return sh ? ((w0 >> sh) | (w1 << (32 - sh))) : w0;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t row_bit(const uint32_t* row, int pos) {
+    return (row[pos >> 5] >> (pos & 31)) & 1u;
+}
+
+// Slow path of the window: the block's ends are near a rounding boundary or
+// on both sides of one.  V_j = 31 v0 + d j (d = v1 - v0) is 31 v(j) exactly
+// interpolated; the cell of each j is decided from V_j when it is at least
+// 31 M from a boundary, else by the exact FP64 expression (exact_o(j) returns
+// floor(F_j + F_j D + 1/2) - floor(F_j)).  path: 1 = single clean crossing,
+// 2 = per-template decision.  Bits whose position falls outside the staged
+// row set *bad and read as 0.
+template <class ExactO>
+__host__ __device__ uint32_t fp_window_slow(int v0, int v1, int pbase, int pos_max, int s,
+                                            int M, const uint32_t* row, ExactO exact_o,
+                                            int* path, bool* bad) {
+    const long long d = (long long)v1 - (long long)v0;
+    const long long S31 = 31LL << s;
+    const long long M31 = 31LL * M;
+    const int vmin = imin(v0, v1), vmax = imax(v0, v1);
+    const int ca = vmin >> s, cb = vmax >> s;
+    if (cb == ca + 1) {
+        const long long lo_edge = (long long)ca << s;
+        const long long Bc = (long long)cb << s;
+        const long long hi_edge = ((long long)cb + 1) << s;
+        if ((long long)vmin - lo_edge >= M && hi_edge - (long long)vmax >= M) {
+            const long long num = 31LL * (Bc - (long long)v0);
+            int jc;
+            if (d > 0) jc = (int)((num + d - 1) / d);        // first j with V_j >= 31 Bc
+            else jc = (int)((-num) / (-d)) + 1;               // first j with V_j < 31 Bc
+            if (jc >= 1 && jc <= 31) {
+                const long long B31 = 31LL * Bc;
+                const long long Vm = 31LL * v0 + d * (jc - 1);
+                const long long Vp = 31LL * v0 + d * jc;
+                const long long dm = Vm > B31 ? Vm - B31 : B31 - Vm;
+                const long long dp = Vp > B31 ? Vp - B31 : B31 - Vp;
+                if (dm >= M31 && dp >= M31) {
+                    const int o0 = v0 >> s;
+                    const int o1 = d > 0 ? o0 + 1 : o0 - 1;
+                    const int p0 = pbase + o0, p1 = pbase + o1;
+                    if ((unsigned)p0 <= (unsigned)pos_max && (unsigned)p1 <= (unsigned)pos_max) {
+                        const uint32_t low = (1u << jc) - 1u;
+                        *path = 1;
+                        return (row_window(row, p0) & low) | (row_window(row, p1) & ~low);
+                    }
+                }
+            }
+        }
+    }
+    *path = 2;
+    uint32_t m = 0;
+    const long long base = 31LL * ((long long)ca << s);
+    for (int j = 0; j < 32; ++j) {
+        const long long V = 31LL * v0 + d * j;
+        long long rel = V - base;                 // >= 0
+        int q = ca;
+        while (rel >= S31) { rel -= S31; ++q; }
+        int o;
+        if (rel < M31 || rel > S31 - M31) o = exact_o(j);
+        else o = q;
+        const int pos = pbase + j + o;
+        if (pos < 0 || pos >= pos_max + 33) { *bad = true; continue; }
+        m |= row_bit(row, pos) << j;
+    }
+    return m;
+}
+
+
+// Raises a kernel's dynamic shared-memory limit once (never inside a graph
+// capture once the first eager launch has set it).
+template <class K>
+inline void ensure_smem(K kernel, int bytes, int* done) {
+    if (bytes > *done) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        *done = bytes;
+    }
+}
+
+// ---------------------------------------------------------------- launches
+struct CountArgs {
+    const ProbDev* probs;        // device array [n_probs]
+    int n_probs;
+    const int64_t* cta_item;     // [ctas + 1] item range per CTA
+    const int32_t* cta_visit;    // [ctas] first visit index per CTA
+    Entry* visit_buf;            // [visits][cap]
+    int32_t* visit_count;        // [visits]
+    int cap;                     // entries per visit buffer
+    int top_k;
+    int dense;                   // write dense counts instead of toplists
+    int32_t* const* dense_unw;   // device array [n_probs] of device pointers
+    float* const* dense_w;
+    unsigned* status;
+    int chunk;                   // SFTs per stage
+    int smem_bytes;
+    int wseg_max, ot_max;
+    int mode;                    // BSH_MODE_*
+};
+
+struct TmapSet {
+    alignas(64) unsigned char map[MAX_PROBLEMS][128];
+};
+
+void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st);
+void launch_tables(const ProbDev& hp, const ProbDev* dprob, int mode, unsigned* status, cudaStream_t st);
+void launch_peakgram(const float* power, int N, int K, int window, double rho_th, float* rho,
+                     uint32_t* bits, int W, cudaStream_t st);
+int launch_weights(const double* sky, int S, const double* arms, const double* Sn, int N, int norm,
+                   int dtype, void* w, double* sum_w, double* sum_w2, unsigned* status, cudaStream_t st);
+
+struct MergeArgs {
+    const ProbDev* probs;
+    int n_probs;
+    const int32_t* region_problem;   // [regions]
+    const int32_t* region_visit_off; // [regions + 1]
+    const int32_t* region_visits;    // [sum visits]
+    const Entry* visit_buf;
+    const int32_t* visit_count;
+    int cap, top_k;
+    Entry* scratch;                  // [regions][top_k]
+    bsh_cand* out;
+    int32_t* n_out;
+    unsigned* status;
+};
+void launch_merge(const MergeArgs& a, int regions, cudaStream_t st);
+
+struct PowerArgs {
+    const ProbDev* probs;
+    int n_probs;
+    const int32_t* region_problem;
+    bsh_cand* cands;
+    const int32_t* n_cands;
+    int top_k, n_cf;
+    bsh_cand* final_list;
+    int32_t* n_final;
+    unsigned* status;
+};
+void launch_power(const PowerArgs& a, int regions, cudaStream_t st);
+
+}  // namespace bsh

@@ -1,0 +1,581 @@
+// Number count (Sec. IV.C, Sec. V.A; track of Eq. (15); significance of
+// Eq. (25)) with a fused per-patch toplist.
+//
+// Work decomposition: an item is (problem q, sky point s, f0 block fb of 32
+// templates, binary tile bt of THREADS binary templates).  Each thread owns
+// one binary template and the 32 f0 templates of the block: for every SFT the
+// track of all 32 f0 templates is one contiguous 32-bit window of the
+// peakgram row (consecutive f0 bins, offset constant except at most one
+// boundary crossing inside the block), so one shared-memory funnel shift
+// yields 32 terms.  Unweighted counts accumulate in bit-sliced carry-save
+// counters; weighted counts in FP32 per 32-SFT block, Kahan-compensated across
+// blocks.  Persistent CTAs walk a static, cost-balanced range of items; the
+// peakgram band and the per-SFT tables of each SFT chunk are staged into
+// shared memory by TMA (cp.async.bulk.tensor / cp.async.bulk) one chunk ahead.
+//
+// The plain form (BSH_MODE_PLAIN) evaluates the FP64 track for every term,
+// sums FP64 weights in FP64, and runs once per sky patch.
+#include <cuda.h>
+
+#include "bsh_internal.cuh"
+#include "select.cuh"
+
+namespace bsh {
+namespace {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait on an mbarrier phase: false after ~2^22 polls (seconds).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------ items
+struct Item {
+    int q, s, fb, bt;
+};
+
+__device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
+    int q = 0;
+    while (q + 1 < a.n_probs && it >= a.probs[q + 1].item_begin) ++q;
+    const ProbDev& P = a.probs[q];
+    const long long loc = it - P.item_begin;
+    const long long per_s = (long long)P.n_fb * P.n_bt;
+    Item r;
+    r.q = q;
+    r.s = (int)(loc / per_s);
+    const int rr = (int)(loc % per_s);
+    r.fb = rr / P.n_bt;
+    r.bt = rr % P.n_bt;
+    return r;
+}
+
+// Shared-memory layout of the batched kernel.
+struct Layout {
+    int pk[2], vn[2], w[2], c[2], y, cp, bar, sel, misc, total;
+};
+
+__host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
+
+__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max) {
+    Layout L;
+    int o = 0;
+    for (int b = 0; b < 2; ++b) { L.pk[b] = o; o = align128(o + I * wseg * 4); }
+    for (int b = 0; b < 2; ++b) { L.vn[b] = o; o = align128(o + I * 4); }
+    for (int b = 0; b < 2; ++b) { L.w[b] = o; o = align128(o + I * 4); }
+    for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + I * ot_max * 4); }
+    L.y = o; o = align128(o + I * 8);
+    L.cp = o; o = align128(o + I * ot_max * 8);
+    L.bar = o; o = align128(o + 16);
+    L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
+    L.misc = o; o = align128(o + 64);
+    L.total = o;
+    return L;
+}
+
+struct TopSmem {
+    unsigned long long tau;
+    int count;
+    int have_tau;
+    float mean, inv_sig;
+};
+
+// Per-item constants shared by every thread.
+struct ItemCtx {
+    int q, s, fb, bt, j0, jb, c0, pbase, ot0, nrows, F2a, region, nchunks;
+    uint32_t lid_base;
+};
+
+__device__ __forceinline__ ItemCtx item_ctx(const CountArgs& a, const Item& it, int THREADS) {
+    const ProbDev& P = a.probs[it.q];
+    ItemCtx c;
+    c.q = it.q;
+    c.s = it.s;
+    c.fb = it.fb;
+    c.bt = it.bt;
+    c.j0 = it.fb * P.JB;
+    c.jb = imin(P.JB, P.n_f0 - c.j0);
+    const int Gj0 = P.G0 + c.j0;
+    int lo_bin = Gj0 + P.o_min - 1 - P.k_lo;
+    lo_bin = lo_bin < 0 ? 0 : lo_bin;
+    c.c0 = (lo_bin >> 5) & ~3;
+    c.pbase = Gj0 - P.k_lo - 32 * c.c0;
+    const int b0 = it.bt * THREADS;
+    const int b1 = imin(b0 + THREADS, P.B) - 1;
+    c.ot0 = b0 / P.n_ap;
+    c.nrows = b1 / P.n_ap - c.ot0 + 1;
+    c.F2a = (int)llrint(2.0 * P.F0) + 2 * c.j0;
+    const int patch = P.patch_of_s[it.s];
+    c.region = P.region_base + patch;
+    c.lid_base = (uint32_t)((long long)(it.s - (int)P.patch_start[patch]) * P.B);
+    c.nchunks = (P.N + a.chunk - 1) / a.chunk;
+    return c;
+}
+
+// Issues the TMA / bulk copies of chunk `ch` of item `c` into buffer `buf`.
+__device__ __forceinline__ void issue_stage(const CountArgs& a, const TmapSet& maps, const ItemCtx& c, int ch,
+                                            unsigned char* smem, const Layout& L, int buf) {
+    const ProbDev& P = a.probs[c.q];
+    const int I = a.chunk;
+    const int i0 = ch * I;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar) + buf;
+    const uint32_t bytes = (uint32_t)(I * a.wseg_max * 4 + I * 4 * 2 + c.nrows * I * 4);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_2d(smem + L.pk[buf], maps.map[c.q], bar, c.c0, i0);
+    bulk_load(smem + L.vn[buf], P.vn_q + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
+    bulk_load(smem + L.w[buf], P.w32 + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
+    for (int r = 0; r < c.nrows; ++r)
+        bulk_load(smem + L.c[buf] + r * I * 4, P.c_q + (size_t)(c.ot0 + r) * P.Np + i0, (uint32_t)(I * 4), bar);
+}
+
+__device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// Exact FP64 fallback for one template block at one SFT (rare).
+__device__ __noinline__ uint32_t slow_window(const ProbDev& P, int v0, int v1, int pbase, int pos_max,
+                                             const uint32_t* row, int s, int b, int i, int j0,
+                                             unsigned* status) {
+    bool have = false;
+    double D = 0.0;
+    auto exact_o = [&](int j) -> int {
+        if (!have) {
+            const double* n = P.sky + 3 * (size_t)s;
+            const double* v = P.v + 3 * (size_t)i;
+            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])),
+                                        __dmul_rn(v[2], n[2]));
+            const int iap = b % P.n_ap;
+            const int ot = b / P.n_ap;
+            const double c = P.c64[(size_t)ot * P.Np + i];
+            D = __dsub_rn(vn, __dmul_rn(P.a_p[iap], c));
+            have = true;
+        }
+        const double F = P.F0 + (double)(j0 + j);
+        const double x = __dadd_rn(F, __dmul_rn(F, D));
+        const double k = floor(__dadd_rn(x, 0.5));
+        return (int)((long long)k - (long long)(P.G0 + j0 + j));
+    };
+    int path = 0;
+    bool bad = false;
+    const uint32_t m = fp_window_slow(v0, v1, pbase, pos_max, P.fp.s_y, P.fp.M, row, exact_o, &path, &bad);
+    if (bad) set_status(status, ST_RANGE);
+    return m;
+}
+
+// ------------------------------------------------------------ toplist pieces
+template <int THREADS>
+__device__ void topk_reduce(const CountArgs& a, Entry* buf, int keep, TopSmem& ts, SelectSmem& sm) {
+    const int n = ts.count;
+    __syncthreads();
+    if (n <= keep) return;
+    auto seg = [&](int, const Entry*& base, int& cnt) {
+        base = buf;
+        cnt = n;
+    };
+    const unsigned long long tau = cta_kth_largest<THREADS>(1, seg, keep, sm);
+    const int m = cta_compact_ge<THREADS>(buf, n, tau, sm);
+    if (threadIdx.x == 0) {
+        ts.count = m;
+        ts.tau = tau;
+        ts.have_tau = 1;
+    }
+    __syncthreads();
+}
+
+template <int THREADS>
+__device__ void topk_close_visit(const CountArgs& a, int visit, TopSmem& ts, SelectSmem& sm) {
+    if (visit < 0) return;
+    Entry* buf = a.visit_buf + (size_t)visit * a.cap;
+    topk_reduce<THREADS>(a, buf, a.top_k, ts, sm);
+    if (threadIdx.x == 0) {
+        a.visit_count[visit] = ts.count;
+        ts.count = 0;
+        ts.have_tau = 0;
+        ts.tau = 0ull;
+    }
+    __syncthreads();
+}
+
+// Scores the 32 templates of this thread and appends the ones above the
+// running threshold; returns after the CTA-wide bookkeeping.
+template <int THREADS>
+__device__ void emit_item(const CountArgs& a, const ProbDev& P, const ItemCtx& c, int b, bool bvalid,
+                          const float* nw, const uint32_t* nu, int visit, TopSmem& ts, SelectSmem& sm) {
+    const int jb = c.jb;
+    if (a.dense) {
+        if (bvalid) {
+            const size_t base = ((size_t)c.s * P.B + b) * P.n_f0 + c.j0;
+            int32_t* du = a.dense_unw[c.q];
+            float* dw = a.dense_w[c.q];
+#pragma unroll
+            for (int j = 0; j < JW; ++j)
+                if (j < jb) {
+                    du[base + j] = (int32_t)nu[j];
+                    dw[base + j] = nw[j];
+                }
+        }
+        return;
+    }
+    Entry* buf = a.visit_buf + (size_t)visit * a.cap;
+    const float mean = ts.mean, isg = ts.inv_sig;
+    const unsigned long long tau = ts.tau;
+    const bool have = ts.have_tau != 0;
+    if (bvalid) {
+        const uint32_t lid0 = (c.lid_base + (uint32_t)b) * (uint32_t)P.n_f0 + (uint32_t)c.j0;
+#pragma unroll
+        for (int j = 0; j < JW; ++j) {
+            if (j < jb) {
+                const float sc = (nw[j] - mean) * isg;
+                const unsigned long long key = make_key(sc, lid0 + (uint32_t)j);
+                if (!have || key > tau) {
+                    const int pos = atomicAdd(&ts.count, 1);
+                    Entry e;
+                    e.key = key;
+                    e.n_w = nw[j];
+                    e.n_unw = (int32_t)nu[j];
+                    buf[pos] = e;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (ts.count > a.cap - THREADS * JW) topk_reduce<THREADS>(a, buf, a.top_k, ts, sm);
+}
+
+// ------------------------------------------------------------ batched kernel
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
+    SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem + L.sel);
+    TopSmem& ts = *reinterpret_cast<TopSmem*>(smem + L.misc);
+    const int tid = threadIdx.x;
+    const int I = a.chunk;
+
+    long long it = a.cta_item[blockIdx.x];
+    const long long it_end = a.cta_item[blockIdx.x + 1];
+    if (it >= it_end) return;
+    int visit = a.cta_visit[blockIdx.x] - 1;
+    int region = -1;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        ts.count = 0;
+        ts.have_tau = 0;
+        ts.tau = 0ull;
+    }
+    __syncthreads();
+
+    ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
+    if (tid == 0) issue_stage(a, maps, cur, 0, smem, L, 0);
+    unsigned g = 0;   // chunk sequence number within this CTA
+
+    while (true) {
+        const ProbDev& P = a.probs[cur.q];
+        const int b = cur.bt * THREADS + tid;
+        const bool bvalid = b < P.B;
+        const int iap = bvalid ? b % P.n_ap : 0;
+        const int ot = bvalid ? b / P.n_ap - cur.ot0 : 0;
+        const int apq = bvalid ? P.ap_q[iap] : 0;
+        const uint32_t jmask = bvalid ? (cur.jb >= 32 ? 0xffffffffu : ((1u << cur.jb) - 1u)) : 0u;
+        const int s_y = P.fp.s_y, M = P.fp.M;
+        const int wseg = a.wseg_max;
+        const int pos_max = 32 * wseg - 33;
+        const int ot_max = a.ot_max;
+
+        // new region -> new visit buffer
+        if (!a.dense && cur.region != region) {
+            topk_close_visit<THREADS>(a, visit, ts, sm);
+            ++visit;
+            region = cur.region;
+        }
+        if (tid == 0) {
+            const double sw = P.sum_w[cur.s], sw2 = P.sum_w2[cur.s];
+            const double var = P.p_th * (1.0 - P.p_th) * sw2;
+            ts.mean = (float)(P.p_th * sw);
+            ts.inv_sig = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
+        }
+
+        float part[JW], acc[JW], comp[JW];
+#pragma unroll
+        for (int j = 0; j < JW; ++j) { part[j] = 0.f; acc[j] = 0.f; comp[j] = 0.f; }
+        uint32_t ones = 0, twos = 0, fours = 0;
+        uint32_t e8[13];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) e8[k] = 0;
+
+        const int F2a = cur.F2a, F2b = cur.F2a + 62;
+        for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
+            const int buf = g & 1;
+            const bool ok = mbar_wait(&bars[buf], (g >> 1) & 1);
+            if (__syncthreads_or(!ok)) {      // every thread leaves together
+                if (tid == 0) set_status(a.status, ST_TIMEOUT);
+                return;
+            }
+            // tables of this chunk: Z and C_q at j0 and j0 + 31
+            const int32_t* vnr = reinterpret_cast<const int32_t*>(smem + L.vn[buf]);
+            const int32_t* cr = reinterpret_cast<const int32_t*>(smem + L.c[buf]);
+            int2* yp = reinterpret_cast<int2*>(smem + L.y);
+            int2* cp = reinterpret_cast<int2*>(smem + L.cp);
+            for (int e = tid; e < I; e += THREADS) {
+                const int vq = vnr[e];
+                yp[e] = make_int2(make_Z(F2a, vq, P.fp), make_Z(F2b, vq, P.fp));
+            }
+            for (int e = tid; e < I * cur.nrows; e += THREADS) {
+                const int r = e / I, il = e - r * I;
+                const int cq = cr[e];
+                cp[il * ot_max + r] = make_int2(make_C(F2a, cq, P.fp), make_C(F2b, cq, P.fp));
+            }
+            __syncthreads();
+            // prefetch the next chunk (or the next item's first chunk)
+            if (tid == 0) {
+                if (ch + 1 < cur.nchunks) {
+                    issue_stage(a, maps, cur, ch + 1, smem, L, buf ^ 1);
+                } else if (it + 1 < it_end) {
+                    const ItemCtx nx = item_ctx(a, decode_item(a, it + 1), THREADS);
+                    issue_stage(a, maps, nx, 0, smem, L, buf ^ 1);
+                }
+            }
+            const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
+            const float* wt = reinterpret_cast<const float*>(smem + L.w[buf]);
+            const int i0 = ch * I;
+            const int nv = imin(I, P.N - i0);
+            for (int g8 = 0; g8 < I; g8 += 8) {
+                uint32_t mk[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int il = g8 + u;
+                    const int2 z = yp[il];
+                    const int2 cc = cp[il * ot_max + ot];
+                    const int v0 = z.x - __mulhi(apq, cc.x);
+                    const int v1 = z.y - __mulhi(apq, cc.y);
+                    const int pos = cur.pbase + (v0 >> s_y);
+                    const uint32_t* row = pk + il * wseg;
+                    uint32_t m;
+                    if (fp_fast(v0, v1, s_y, M) && (unsigned)pos <= (unsigned)pos_max) {
+                        m = row_window(row, pos);
+                    } else if (il < nv && bvalid) {
+                        m = slow_window(P, v0, v1, cur.pbase, pos_max, row, cur.s, b, i0 + il, cur.j0, a.status);
+                    } else {
+                        m = 0u;
+                    }
+                    m = (il < nv) ? (m & jmask) : 0u;
+                    mk[u] = m;
+                    const float wv = wt[il];
+#pragma unroll
+                    for (int j = 0; j < JW; ++j)
+                        if (m & (1u << j)) part[j] += wv;
+                }
+                uint32_t tA, tB, fA, fB, eights;
+                csa(tA, ones, ones, mk[0], mk[1]);
+                csa(tB, ones, ones, mk[2], mk[3]);
+                csa(fA, twos, twos, tA, tB);
+                csa(tA, ones, ones, mk[4], mk[5]);
+                csa(tB, ones, ones, mk[6], mk[7]);
+                csa(fB, twos, twos, tA, tB);
+                csa(eights, fours, fours, fA, fB);
+#pragma unroll
+                for (int k = 0; k < 13; ++k) {
+                    const uint32_t t = e8[k] & eights;
+                    e8[k] ^= eights;
+                    eights = t;
+                }
+                if ((g8 & 31) == 24) {   // every 32 SFTs: fold the block sums into the Kahan sums
+#pragma unroll
+                    for (int j = 0; j < JW; ++j) {
+                        const float y = part[j] - comp[j];
+                        const float t = acc[j] + y;
+                        comp[j] = (t - acc[j]) - y;
+                        acc[j] = t;
+                        part[j] = 0.f;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // fold the last partial block
+        float nw[JW];
+        uint32_t nu[JW];
+#pragma unroll
+        for (int j = 0; j < JW; ++j) {
+            const float y = part[j] - comp[j];
+            const float t = acc[j] + y;
+            const float cpn = (t - acc[j]) - y;
+            nw[j] = t - cpn;
+            uint32_t cnt = ((ones >> j) & 1u) + 2u * ((twos >> j) & 1u) + 4u * ((fours >> j) & 1u);
+#pragma unroll
+            for (int k = 0; k < 13; ++k) cnt += ((e8[k] >> j) & 1u) << (3 + k);
+            nu[j] = cnt;
+        }
+        __syncthreads();   // ts.mean / ts.inv_sig visible
+        emit_item<THREADS>(a, P, cur, b, bvalid, nw, nu, visit, ts, sm);
+
+        ++it;
+        if (it >= it_end) break;
+        cur = item_ctx(a, decode_item(a, it), THREADS);
+        __syncthreads();
+    }
+    if (!a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+}
+
+// ------------------------------------------------------------ plain kernel
+// FP64 track for every term and FP64 weighted sums; one launch per patch.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem);
+    TopSmem& ts = *reinterpret_cast<TopSmem*>(smem + align128((int)sizeof(SelectSmem)));
+    const int tid = threadIdx.x;
+    long long it = a.cta_item[blockIdx.x];
+    const long long it_end = a.cta_item[blockIdx.x + 1];
+    if (it >= it_end) return;
+    int visit = a.cta_visit[blockIdx.x] - 1;
+    int region = -1;
+    if (tid == 0) {
+        ts.count = 0;
+        ts.have_tau = 0;
+        ts.tau = 0ull;
+    }
+    __syncthreads();
+    for (; it < it_end; ++it) {
+        const ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
+        const ProbDev& P = a.probs[cur.q];
+        const int b = cur.bt * THREADS + tid;
+        const bool bvalid = b < P.B;
+        if (!a.dense && cur.region != region) {
+            topk_close_visit<THREADS>(a, visit, ts, sm);
+            ++visit;
+            region = cur.region;
+        }
+        if (tid == 0) {
+            const double sw = P.sum_w[cur.s], sw2 = P.sum_w2[cur.s];
+            const double var = P.p_th * (1.0 - P.p_th) * sw2;
+            ts.mean = (float)(P.p_th * sw);
+            ts.inv_sig = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
+        }
+        double accw[JW];
+        uint32_t cnt[JW];
+#pragma unroll
+        for (int j = 0; j < JW; ++j) { accw[j] = 0.0; cnt[j] = 0u; }
+        if (bvalid) {
+            const int iap = b % P.n_ap, otg = b / P.n_ap;
+            const double ap = P.a_p[iap];
+            const double* n = P.sky + 3 * (size_t)cur.s;
+            for (int i = 0; i < P.N; ++i) {
+                const double* v = P.v + 3 * (size_t)i;
+                const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])),
+                                            __dmul_rn(v[2], n[2]));
+                const double D = __dsub_rn(vn, __dmul_rn(ap, P.c64[(size_t)otg * P.Np + i]));
+                const double wv = P.w64[(size_t)cur.s * P.Np + i];
+                const uint32_t* row = P.bits + (size_t)i * P.W;
+#pragma unroll
+                for (int j = 0; j < JW; ++j) {
+                    if (j < cur.jb) {
+                        const double F = P.F0 + (double)(cur.j0 + j);
+                        const double x = __dadd_rn(F, __dmul_rn(F, D));
+                        const long long k = (long long)floor(__dadd_rn(x, 0.5));
+                        const long long col = k - P.k_lo;
+                        uint32_t bit = 0u;
+                        if (col >= 0 && col < P.K) bit = (__ldg(row + (col >> 5)) >> (col & 31)) & 1u;
+                        else set_status(a.status, ST_RANGE);
+                        cnt[j] += bit;
+                        if (bit) accw[j] = __dadd_rn(accw[j], wv);
+                    }
+                }
+            }
+        }
+        float nw[JW];
+        uint32_t nu[JW];
+#pragma unroll
+        for (int j = 0; j < JW; ++j) { nw[j] = (float)accw[j]; nu[j] = cnt[j]; }
+        __syncthreads();
+        emit_item<THREADS>(a, P, cur, b, bvalid, nw, nu, visit, ts, sm);
+        __syncthreads();
+    }
+    if (!a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+}
+
+}  // namespace
+
+int count_smem_bytes(int mode, int I, int wseg, int ot_max) {
+    if (mode == BSH_MODE_PLAIN) return align128((int)sizeof(SelectSmem)) + align128((int)sizeof(TopSmem));
+    return make_layout(I, wseg, ot_max).total;
+}
+
+void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st) {
+    if (grid <= 0) return;
+    if (a.mode == BSH_MODE_PLAIN) {
+        if (threads == 128) {
+            static int s_count_plain128 = 0;
+            ensure_smem(count_plain<128>, a.smem_bytes, &s_count_plain128);
+            count_plain<128><<<grid, 128, a.smem_bytes, st>>>(a);
+        } else {
+            static int s_count_plain256 = 0;
+            ensure_smem(count_plain<256>, a.smem_bytes, &s_count_plain256);
+            count_plain<256><<<grid, 256, a.smem_bytes, st>>>(a);
+        }
+        return;
+    }
+    if (threads == 128) {
+        static int s_count_batched128 = 0;
+            ensure_smem(count_batched<128>, a.smem_bytes, &s_count_batched128);
+        count_batched<128><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+    } else {
+        static int s_count_batched256 = 0;
+            ensure_smem(count_batched<256>, a.smem_bytes, &s_count_batched256);
+        count_batched<256><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+    }
+}
+
+}  // namespace bsh

@@ -1,0 +1,803 @@
+// C ABI of libbsh: argument validation, fixed-point scale selection, the
+// static persistent schedule, workspace layout, launches, status, graphs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "bsh_internal.cuh"
+
+namespace bsh {
+int count_smem_bytes(int mode, int I, int wseg, int ot_max);
+}
+
+using namespace bsh;
+
+namespace {
+
+__device__ unsigned g_status_word;
+
+constexpr int kVersion = 10000;
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? BSH_OK : BSH_ERR_CUDA; }
+
+// Device address of the status word for the current device (looked up once per device).
+unsigned* status_ptr() {
+    static std::mutex mu;
+    static unsigned* ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<unsigned*>(p);
+    }
+    return ptrs[dev];
+}
+
+int ceil_log2(double x) {
+    int e = 0;
+    double p = 1.0;
+    if (x <= 1.0) {
+        while (p / 2.0 >= x && e > -200) { p /= 2.0; --e; }
+        return e;
+    }
+    while (p < x && e < 200) { p *= 2.0; ++e; }
+    return e;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Fixed-point scales for the track of one problem (see bsh_internal.cuh).
+int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max, double phi, FixedPoint* fp) {
+    const double ymax = F_max * (v_max + ap_max * Om_max) + 2.0;
+    fp->s_vn = 30 - ceil_log2(v_max * (1.0 + 1e-9));
+    fp->s_c = 30 - ceil_log2(Om_max * (1.0 + 1e-9));
+    fp->s_a = 30 - ceil_log2(std::max(ap_max, 1.0 / 1048576.0) * (1.0 + 1e-12));
+    const double C_max = F_max * Om_max * (1.0 + 1e-9);
+    const int sC_cap = 30 - ceil_log2(C_max);
+    fp->s_y = std::min(30 - ceil_log2(ymax), fp->s_a + sC_cap - 32);
+    fp->s_C = fp->s_y + 32 - fp->s_a;
+    fp->sh_v = fp->s_vn + 1 - fp->s_y;
+    fp->sh_c = fp->s_c + 1 - fp->s_C;
+    if (fp->s_y < 18 || fp->sh_v < 0 || fp->sh_c < 0 || fp->sh_v > 62 || fp->sh_c > 62) return BSH_ERR_RANGE;
+    fp->off_q = (int)std::llround((phi + 0.5) * std::ldexp(1.0, fp->s_y));
+    // error bound of v in units of 2^-s_y (see bsh_internal.cuh)
+    const double u = std::ldexp(1.0, fp->s_y);
+    const double eZ = 0.5 + F_max * std::ldexp(1.0, -fp->s_vn - 1) * u;
+    const double eC = 0.5 + F_max * std::ldexp(1.0, -fp->s_c - 1) * std::ldexp(1.0, fp->s_C);
+    const double ea = 0.5;
+    const double prod = (ap_max * std::ldexp(1.0, fp->s_a) * eC + C_max * std::ldexp(1.0, fp->s_C) * ea + ea * eC) /
+                        4294967296.0;
+    const double cosulp = F_max * Om_max * ap_max * 4.0e-16 * u;   // libm-level differences of cos
+    fp->eps = eZ + 1.0 + prod + cosulp + 1.0;
+    fp->M = (int)std::ceil(2.0 * fp->eps) + 4;
+    if (fp->M * 8 > (1 << fp->s_y)) return BSH_ERR_RANGE;
+    return BSH_OK;
+}
+
+struct ProbHost {
+    bsh_problem d;                         // caller descriptor (device pointers)
+    std::vector<double> ap, Om, Tasc;
+    std::vector<int64_t> ps;
+    std::vector<int32_t> patch_of_s, ap_q;
+    ProbDev pd;                            // filled at create (sizes) and bind (pointers)
+    size_t off_ap, off_apq, off_Om, off_Tasc, off_ps, off_pos, off_vnq, off_cq, off_c64, off_w;
+};
+
+}  // namespace
+
+struct bsh_plan {
+    int n = 0;
+    std::vector<ProbHost> P;
+    bsh_count_options opt{};
+    int mode = BSH_MODE_BATCHED;
+    int threads = 256, chunk = 128, ctas = 0, num_sms = 152;
+    int wseg_max = 4, ot_max = 1, smem = 0, cap = 0, top_k = 1000;
+    int regions = 0, visits = 0;
+    std::vector<int64_t> cta_item;
+    std::vector<int32_t> cta_visit;
+    std::vector<int32_t> region_problem, region_visit_off, region_visits;
+    // plain mode: per-region schedules
+    std::vector<int32_t> pl_off, pl_ctas;
+    // workspace layout
+    size_t off_probs = 0, off_cta_item = 0, off_cta_visit = 0, off_vbuf = 0, off_vcount = 0;
+    size_t off_rprob = 0, off_rvoff = 0, off_rvis = 0, off_scratch = 0, off_dense = 0, ws_size = 0;
+    unsigned char* ws = nullptr;
+    bool bound = false;
+    TmapSet maps{};
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const void* g_args[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int g_ncf = 0;
+};
+
+namespace {
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+int build_schedule(bsh_plan* p);
+
+int validate_problem(const bsh_problem& d) {
+    if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || d.W % 4 != 0) return BSH_ERR_ARG;
+    if (!d.bits || !d.w || !d.sum_w || !d.sum_w2 || !d.v || !d.t || !d.sky) return BSH_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d.bits) % 16 != 0) return BSH_ERR_ARG;
+    if (d.w_dtype < BSH_F64 || d.w_dtype > BSH_BF16) return BSH_ERR_ARG;
+    if (d.n_f0 <= 0 || d.S <= 0 || d.n_patch <= 0 || !d.patch_start) return BSH_ERR_ARG;
+    if (d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || !d.a_p || !d.Omega || !d.T_asc) return BSH_ERR_ARG;
+    if (!finite_pos(d.v_max) || !std::isfinite(d.F0) || d.F0 <= 0.0) return BSH_ERR_ARG;
+    const double F2 = 2.0 * d.F0;
+    if (F2 != std::floor(F2) || F2 + 2.0 * (d.n_f0 + 64) > 2147483000.0) return BSH_ERR_ARG;
+    if (!(d.rho_th > 0.0) || !std::isfinite(d.rho_th)) return BSH_ERR_ARG;
+    if (d.patch_start[0] != 0 || d.patch_start[d.n_patch] != d.S) return BSH_ERR_ARG;
+    for (int p = 0; p < d.n_patch; ++p)
+        if (d.patch_start[p + 1] < d.patch_start[p]) return BSH_ERR_ARG;
+    for (int k = 0; k < d.n_ap; ++k)
+        if (!(d.a_p[k] >= 0.0) || !std::isfinite(d.a_p[k])) return BSH_ERR_ARG;
+    for (int k = 0; k < d.n_Om; ++k)
+        if (!finite_pos(d.Omega[k])) return BSH_ERR_ARG;
+    for (int k = 0; k < d.n_Om * d.n_T; ++k)
+        if (!std::isfinite(d.T_asc[k])) return BSH_ERR_ARG;
+    return BSH_OK;
+}
+
+int prepare_problem(bsh_plan* p, ProbHost& h) {
+    const bsh_problem& d = h.d;
+    ProbDev& pd = h.pd;
+    std::memset(&pd, 0, sizeof(pd));
+    pd.N = d.N;
+    pd.K = d.K;
+    pd.W = d.W;
+    pd.k_lo = d.k_lo;
+    pd.n_f0 = d.n_f0;
+    pd.S = d.S;
+    pd.n_ap = d.n_ap;
+    pd.n_Om = d.n_Om;
+    pd.n_T = d.n_T;
+    pd.nOT = d.n_Om * d.n_T;
+    const long long B = (long long)d.n_ap * pd.nOT;
+    if (B > (1LL << 30)) return BSH_ERR_RANGE;
+    pd.B = (int)B;
+    pd.n_patch = d.n_patch;
+    pd.w_dtype = d.w_dtype;
+    pd.F0 = d.F0;
+    pd.G0 = (int)std::floor(d.F0);
+    const int nb = (d.n_f0 + JW - 1) / JW;
+    pd.JB = (d.n_f0 + nb - 1) / nb;
+    pd.n_fb = (d.n_f0 + pd.JB - 1) / pd.JB;
+    pd.n_bt = (pd.B + p->threads - 1) / p->threads;
+    pd.p_th = std::exp(-d.rho_th);
+    pd.v_max = d.v_max;
+    // patch template counts must fit a 32-bit local id
+    for (int q = 0; q < d.n_patch; ++q) {
+        const double nt = (double)(h.ps[q + 1] - h.ps[q]) * (double)B * d.n_f0;
+        if (nt >= 4294967295.0) return BSH_ERR_RANGE;
+    }
+    double ap_max = 0.0, Om_max = 0.0;
+    for (double a : h.ap) ap_max = std::max(ap_max, a);
+    for (double o : h.Om) Om_max = std::max(Om_max, o);
+    const int j_last = (pd.n_fb - 1) * pd.JB + JW;             // last f0 offset evaluated (+1 for a crossing)
+    const double F_eval = d.F0 + j_last;
+    const double phi = d.F0 - std::floor(d.F0);
+    int rc = choose_fixed_point(F_eval, d.v_max, ap_max, Om_max, phi, &pd.fp);
+    if (rc) return rc;
+    const double ymax = F_eval * (d.v_max + ap_max * Om_max);
+    pd.o_max = (int)std::ceil(ymax) + 2;
+    pd.o_min = -pd.o_max;
+    // band check: every valid template stays inside [k_lo, k_lo + K)
+    const double Fv_max = d.F0 + d.n_f0 - 1;
+    const double yv = Fv_max * (d.v_max + ap_max * Om_max);
+    const long long kmin = (long long)std::floor(d.F0 - yv + 0.5) - 1;
+    const long long kmax = (long long)std::floor(Fv_max + yv + 0.5) + 1;
+    if (kmin < d.k_lo || kmax >= (long long)d.k_lo + d.K) return BSH_ERR_RANGE;
+    // staged segment width
+    int wseg = 4;
+    for (int fb = 0; fb < pd.n_fb; ++fb) {
+        const int Gj0 = pd.G0 + fb * pd.JB;
+        int lo_bin = Gj0 + pd.o_min - 1 - d.k_lo;
+        lo_bin = std::max(lo_bin, 0);
+        const int c0 = (lo_bin >> 5) & ~3;
+        const int hi_bin = Gj0 + 31 + pd.o_max + 1 - d.k_lo;
+        const int w = ((hi_bin >> 5) - c0 + 2 + 3) & ~3;
+        wseg = std::max(wseg, w);
+    }
+    if (wseg > 64) return BSH_ERR_RANGE;
+    pd.Wseg = wseg;
+    // a_p in fixed point
+    h.ap_q.resize(d.n_ap);
+    for (int k = 0; k < d.n_ap; ++k) h.ap_q[k] = (int32_t)std::llround(std::ldexp(h.ap[k], pd.fp.s_a));
+    // patch of each sky point
+    h.patch_of_s.assign(d.S, 0);
+    for (int q = 0; q < d.n_patch; ++q)
+        for (int64_t s = h.ps[q]; s < h.ps[q + 1]; ++s) h.patch_of_s[s] = q;
+    return BSH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsh_error_string(int status) {
+    switch (status) {
+        case BSH_OK: return "ok";
+        case BSH_ERR_ARG: return "invalid argument";
+        case BSH_ERR_RANGE: return "track outside the loaded band or parameter outside the fixed-point range";
+        case BSH_ERR_TIMEOUT: return "bounded device wait expired";
+        case BSH_ERR_CUDA: return "CUDA runtime error";
+        case BSH_ERR_WORKSPACE: return "workspace missing or too small";
+        case BSH_ERR_STATE: return "call order violated";
+        default: return "unknown status";
+    }
+}
+
+int bsh_version(void) { return kVersion; }
+
+int bsh_sync_status(bsh_stream stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BSH_ERR_CUDA;
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, sp, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return BSH_ERR_CUDA;
+    const unsigned zero = 0;
+    if (cudaMemcpy(sp, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return BSH_ERR_CUDA;
+    if (v & ST_TIMEOUT) return BSH_ERR_TIMEOUT;
+    if (v & ST_RANGE) return BSH_ERR_RANGE;
+    if (v & ST_ARG) return BSH_ERR_ARG;
+    return BSH_OK;
+}
+
+int bsh_make_peakgram(const float* power, int N, int K, int median_window, double rho_th, float* rho_out,
+                      uint32_t* bits, int W, bsh_stream stream) {
+    if (N < 0 || K <= 0 || W < (K + 31) / 32 || !bits || (N > 0 && !power)) return BSH_ERR_ARG;
+    if (median_window < 0 || (median_window > 0 && (median_window % 2 == 0 || median_window > K)))
+        return BSH_ERR_ARG;
+    if (median_window > 0 && (size_t)K * sizeof(float) > 200 * 1024) return BSH_ERR_ARG;
+    if (!std::isfinite(rho_th)) return BSH_ERR_ARG;
+    launch_peakgram(power, N, K, median_window, rho_th, rho_out, bits, W, (cudaStream_t)stream);
+    return cuda_fail(cudaGetLastError());
+}
+
+int bsh_weights(const double* sky, int S, const double* arms, const double* Sn, int N, int normalize, int dtype,
+                void* w, double* sum_w, double* sum_w2, bsh_stream stream) {
+    if (S < 0 || N <= 0 || !arms || !Sn || (S > 0 && (!sky || !w))) return BSH_ERR_ARG;
+    if (dtype < BSH_F64 || dtype > BSH_BF16 || (normalize != 0 && normalize != 1)) return BSH_ERR_ARG;
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    launch_weights(sky, S, arms, Sn, N, normalize, dtype, w, sum_w, sum_w2, sp, (cudaStream_t)stream);
+    return cuda_fail(cudaGetLastError());
+}
+
+int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count_options* opt, bsh_plan** out) {
+    if (!out) return BSH_ERR_ARG;
+    *out = nullptr;
+    if (!problems || n_problems < 1 || n_problems > MAX_PROBLEMS || !opt) return BSH_ERR_ARG;
+    if (opt->mode != BSH_MODE_BATCHED && opt->mode != BSH_MODE_PLAIN) return BSH_ERR_ARG;
+    if (opt->top_k < 1 || opt->top_k > 16384) return BSH_ERR_ARG;
+    if (opt->threads != 0 && opt->threads != 128 && opt->threads != 256) return BSH_ERR_ARG;
+    if (opt->sft_chunk != 0 && opt->sft_chunk != 64 && opt->sft_chunk != 128 && opt->sft_chunk != 256)
+        return BSH_ERR_ARG;
+    if (opt->ctas_per_sm < 0 || opt->ctas_per_sm > 8) return BSH_ERR_ARG;
+    for (int q = 0; q < n_problems; ++q) {
+        const int rc = validate_problem(problems[q]);
+        if (rc) return rc;
+    }
+    bsh_plan* p = new bsh_plan();
+    p->n = n_problems;
+    p->opt = *opt;
+    p->mode = opt->mode;
+    p->top_k = opt->top_k;
+    p->threads = opt->threads ? opt->threads : 256;
+    p->chunk = opt->sft_chunk ? opt->sft_chunk : 128;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+        p->num_sms = nsm;
+    else
+        cudaGetLastError();
+    p->P.resize(n_problems);
+    for (int q = 0; q < n_problems; ++q) {
+        ProbHost& h = p->P[q];
+        h.d = problems[q];
+        const bsh_problem& d = problems[q];
+        h.ap.assign(d.a_p, d.a_p + d.n_ap);
+        h.Om.assign(d.Omega, d.Omega + d.n_Om);
+        h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
+        h.ps.assign(d.patch_start, d.patch_start + d.n_patch + 1);
+        h.d.a_p = nullptr;
+        h.d.Omega = nullptr;
+        h.d.T_asc = nullptr;
+        h.d.patch_start = nullptr;
+    }
+    const int rc = build_schedule(p);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return BSH_OK;
+}
+
+void bsh_plan_destroy(bsh_plan* p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
+}
+
+size_t bsh_plan_workspace_size(const bsh_plan* p) { return p ? p->ws_size : 0; }
+int bsh_plan_num_regions(const bsh_plan* p) { return p ? p->regions : 0; }
+int bsh_plan_first_region(const bsh_plan* p, int q) {
+    if (!p || q < 0 || q >= p->n) return -1;
+    return p->P[q].pd.region_base;
+}
+
+}  // extern "C"
+
+namespace {
+
+int build_schedule(bsh_plan* p) {
+    // tile shapes
+    p->ot_max = 1;
+    for (auto& h : p->P) {
+        const int rows = std::min(h.d.n_Om * h.d.n_T, (p->threads + h.d.n_ap - 1) / h.d.n_ap + 1);
+        p->ot_max = std::max(p->ot_max, rows);
+    }
+    int region = 0;
+    long long items = 0;
+    for (auto& h : p->P) {
+        const int rc = prepare_problem(p, h);
+        if (rc) return rc;
+        h.pd.region_base = region;
+        region += h.d.n_patch;
+        p->wseg_max = std::max(p->wseg_max, h.pd.Wseg);
+    }
+    p->regions = region;
+    // chunk size: shrink until the shared-memory layout fits
+    while (true) {
+        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max);
+        if (p->smem <= 220 * 1024 || p->chunk <= 32) break;
+        p->chunk /= 2;
+    }
+    if (p->smem > 220 * 1024) return BSH_ERR_RANGE;
+    std::vector<long long> cum_cost(p->n + 1, 0);
+    for (int q = 0; q < p->n; ++q) {
+        ProbDev& pd = p->P[q].pd;
+        pd.Np = (pd.N + 255) / 256 * 256;
+        pd.item_begin = items;
+        pd.n_items = (long long)pd.S * pd.n_fb * pd.n_bt;
+        pd.cost = (pd.N + p->chunk - 1) / p->chunk + 1;
+        items += pd.n_items;
+        cum_cost[q + 1] = cum_cost[q] + pd.n_items * pd.cost;
+    }
+    const long long total_items = items;
+    const int cps = p->opt.ctas_per_sm ? p->opt.ctas_per_sm : 1;
+    const int k = p->top_k;
+    // region item ranges
+    std::vector<long long> r_begin(p->regions + 1, 0);
+    std::vector<int> r_prob(p->regions);
+    for (int q = 0; q < p->n; ++q) {
+        const ProbDev& pd = p->P[q].pd;
+        const long long per_s = (long long)pd.n_fb * pd.n_bt;
+        for (int pt = 0; pt < pd.n_patch; ++pt) {
+            r_begin[pd.region_base + pt] = pd.item_begin + p->P[q].ps[pt] * per_s;
+            r_prob[pd.region_base + pt] = q;
+        }
+    }
+    r_begin[p->regions] = total_items;
+    p->region_problem.assign(r_prob.begin(), r_prob.end());
+    std::vector<std::vector<int32_t>> rvis(p->regions);
+    if (p->mode == BSH_MODE_BATCHED) {
+        long long C = (long long)p->num_sms * cps;
+        C = std::max(1LL, std::min(C, total_items));
+        p->ctas = (int)C;
+        p->cta_item.assign(C + 1, 0);
+        const long long T = cum_cost[p->n];
+        for (long long c = 0; c <= C; ++c) {
+            const long long X = (long long)((__int128)T * c / C);
+            int q = 0;
+            while (q + 1 < p->n && X >= cum_cost[q + 1]) ++q;
+            long long it = p->P[q].pd.item_begin + (X - cum_cost[q]) / p->P[q].pd.cost;
+            if (c == C) it = total_items;
+            p->cta_item[c] = std::min(it, total_items);
+        }
+        for (long long c = 1; c <= C; ++c) p->cta_item[c] = std::max(p->cta_item[c], p->cta_item[c - 1]);
+        p->cta_visit.assign(C + 1, 0);
+        int v = 0;
+        for (long long c = 0; c < C; ++c) {
+            p->cta_visit[c] = v;
+            const long long a = p->cta_item[c], b = p->cta_item[c + 1];
+            if (a >= b) continue;
+            int r = (int)(std::upper_bound(r_begin.begin(), r_begin.end(), a) - r_begin.begin()) - 1;
+            while (r < p->regions && r_begin[r] < b) {
+                if (r_begin[r + 1] > r_begin[r] && r_begin[r + 1] > a) rvis[r].push_back(v++);
+                ++r;
+            }
+        }
+        p->cta_visit[C] = v;
+        p->visits = v;
+    } else {
+        // one launch per region, each with its own small persistent grid
+        const long long Cmax = (long long)p->num_sms * cps;
+        p->pl_off.assign(p->regions + 1, 0);
+        p->pl_ctas.assign(p->regions, 0);
+        p->cta_item.clear();
+        p->cta_visit.clear();
+        int v = 0;
+        for (int r = 0; r < p->regions; ++r) {
+            const long long a = r_begin[r], b = r_begin[r + 1];
+            const long long n = b - a;
+            const int C = (int)std::max(0LL, std::min(Cmax, n));
+            p->pl_off[r] = (int)p->cta_item.size();
+            p->pl_ctas[r] = C;
+            for (int c = 0; c <= C; ++c) p->cta_item.push_back(C ? a + n * c / C : a);
+            for (int c = 0; c < C; ++c) {
+                p->cta_visit.push_back(v);
+                rvis[r].push_back(v++);
+            }
+            p->cta_visit.push_back(v);
+        }
+        p->pl_off[p->regions] = (int)p->cta_item.size();
+        p->visits = v;
+        p->ctas = (int)Cmax;
+    }
+    p->region_visit_off.assign(p->regions + 1, 0);
+    p->region_visits.clear();
+    for (int r = 0; r < p->regions; ++r) {
+        p->region_visit_off[r] = (int)p->region_visits.size();
+        for (int v : rvis[r]) p->region_visits.push_back(v);
+    }
+    p->region_visit_off[p->regions] = (int)p->region_visits.size();
+    p->cap = 2 * k + p->threads * JW;
+    // workspace layout
+    size_t o = 0;
+    p->off_probs = o; o = al(o + sizeof(ProbDev) * p->n);
+    for (auto& h : p->P) {
+        const ProbDev& pd = h.pd;
+        h.off_ap = o; o = al(o + sizeof(double) * pd.n_ap);
+        h.off_apq = o; o = al(o + sizeof(int32_t) * pd.n_ap);
+        h.off_Om = o; o = al(o + sizeof(double) * pd.n_Om);
+        h.off_Tasc = o; o = al(o + sizeof(double) * pd.nOT);
+        h.off_ps = o; o = al(o + sizeof(int64_t) * (pd.n_patch + 1));
+        h.off_pos = o; o = al(o + sizeof(int32_t) * pd.S);
+        h.off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)pd.S * pd.Np);
+        h.off_cq = o; o = al(o + sizeof(int32_t) * (size_t)pd.nOT * pd.Np);
+        h.off_c64 = o; o = al(o + sizeof(double) * (size_t)pd.nOT * pd.Np);
+        const size_t wsz = p->mode == BSH_MODE_PLAIN ? sizeof(double) : sizeof(float);
+        h.off_w = o; o = al(o + wsz * (size_t)pd.S * pd.Np);
+    }
+    p->off_cta_item = o; o = al(o + sizeof(int64_t) * p->cta_item.size());
+    p->off_cta_visit = o; o = al(o + sizeof(int32_t) * p->cta_visit.size());
+    p->off_vbuf = o; o = al(o + sizeof(Entry) * (size_t)p->visits * p->cap);
+    p->off_vcount = o; o = al(o + sizeof(int32_t) * (size_t)std::max(1, p->visits));
+    p->off_rprob = o; o = al(o + sizeof(int32_t) * p->regions);
+    p->off_rvoff = o; o = al(o + sizeof(int32_t) * (p->regions + 1));
+    p->off_rvis = o; o = al(o + sizeof(int32_t) * std::max<size_t>(1, p->region_visits.size()));
+    p->off_scratch = o; o = al(o + sizeof(Entry) * (size_t)p->regions * k);
+    p->off_dense = o; o = al(o + 2 * sizeof(void*) * p->n);
+    p->ws_size = o;
+    return BSH_OK;
+}
+
+template <class T>
+cudaError_t up(void* dst, const T* src, size_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, st);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int encode_bits_map(bsh_plan* p, int q) {
+    const ProbHost& h = p->P[q];
+    auto enc = get_encode();
+    if (!enc) return BSH_ERR_CUDA;
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(p->maps.map[q]);
+    cuuint64_t dims[2] = {(cuuint64_t)h.d.W, (cuuint64_t)h.d.N};
+    cuuint64_t strides[1] = {(cuuint64_t)h.d.W * 4};
+    cuuint32_t box[2] = {(cuuint32_t)p->wseg_max, (cuuint32_t)p->chunk};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(h.d.bits), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BSH_OK : BSH_ERR_ARG;
+}
+
+CountArgs count_args(bsh_plan* p, int dense) {
+    CountArgs a{};
+    a.probs = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs);
+    a.n_probs = p->n;
+    a.cta_item = reinterpret_cast<const int64_t*>(p->ws + p->off_cta_item);
+    a.cta_visit = reinterpret_cast<const int32_t*>(p->ws + p->off_cta_visit);
+    a.visit_buf = reinterpret_cast<Entry*>(p->ws + p->off_vbuf);
+    a.visit_count = reinterpret_cast<int32_t*>(p->ws + p->off_vcount);
+    a.cap = p->cap;
+    a.top_k = p->top_k;
+    a.dense = dense;
+    a.dense_unw = reinterpret_cast<int32_t* const*>(p->ws + p->off_dense);
+    a.dense_w = reinterpret_cast<float* const*>(p->ws + p->off_dense + sizeof(void*) * p->n);
+    a.status = status_ptr();
+    a.chunk = p->chunk;
+    a.smem_bytes = p->smem;
+    a.wseg_max = p->wseg_max;
+    a.ot_max = p->ot_max;
+    a.mode = p->mode;
+    return a;
+}
+
+int run_count(bsh_plan* p, int dense, cudaStream_t st) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    const ProbDev* dprobs = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs);
+    for (int q = 0; q < p->n; ++q) launch_tables(p->P[q].pd, dprobs + q, p->mode, sp, st);
+    CountArgs a = count_args(p, dense);
+    if (p->mode == BSH_MODE_BATCHED) {
+        launch_count(a, p->maps, p->ctas, p->threads, st);
+    } else {
+        for (int r = 0; r < p->regions; ++r) {
+            if (p->pl_ctas[r] == 0) continue;
+            CountArgs ar = a;
+            ar.cta_item = a.cta_item + p->pl_off[r];
+            ar.cta_visit = a.cta_visit + p->pl_off[r];
+            launch_count(ar, p->maps, p->pl_ctas[r], p->threads, st);
+        }
+    }
+    return cuda_fail(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsh_plan_bind(bsh_plan* p, void* workspace, size_t bytes, bsh_stream stream) {
+    if (!p) return BSH_ERR_ARG;
+    if (!workspace || bytes < p->ws_size) return BSH_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BSH_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    p->ws = static_cast<unsigned char*>(workspace);
+    std::vector<ProbDev> hp(p->n);
+    for (int q = 0; q < p->n; ++q) {
+        ProbHost& h = p->P[q];
+        ProbDev& pd = h.pd;
+        const bsh_problem& d = h.d;
+        pd.bits = d.bits;
+        pd.rho = d.rho;
+        pd.w = d.w;
+        pd.sum_w = d.sum_w;
+        pd.sum_w2 = d.sum_w2;
+        pd.v = d.v;
+        pd.t = d.t;
+        pd.sky = d.sky;
+        pd.a_p = reinterpret_cast<const double*>(p->ws + h.off_ap);
+        pd.ap_q = reinterpret_cast<const int32_t*>(p->ws + h.off_apq);
+        pd.Om = reinterpret_cast<const double*>(p->ws + h.off_Om);
+        pd.Tasc = reinterpret_cast<const double*>(p->ws + h.off_Tasc);
+        pd.patch_start = reinterpret_cast<const int64_t*>(p->ws + h.off_ps);
+        pd.patch_of_s = reinterpret_cast<const int32_t*>(p->ws + h.off_pos);
+        pd.vn_q = reinterpret_cast<int32_t*>(p->ws + h.off_vnq);
+        pd.c_q = reinterpret_cast<int32_t*>(p->ws + h.off_cq);
+        pd.c64 = reinterpret_cast<double*>(p->ws + h.off_c64);
+        if (p->mode == BSH_MODE_PLAIN) {
+            pd.w64 = reinterpret_cast<double*>(p->ws + h.off_w);
+            pd.w32 = nullptr;
+        } else {
+            pd.w32 = reinterpret_cast<float*>(p->ws + h.off_w);
+            pd.w64 = nullptr;
+        }
+        hp[q] = pd;
+        cudaError_t e = cudaSuccess;
+        e = e ? e : up(p->ws + h.off_ap, h.ap.data(), h.ap.size(), st);
+        e = e ? e : up(p->ws + h.off_apq, h.ap_q.data(), h.ap_q.size(), st);
+        e = e ? e : up(p->ws + h.off_Om, h.Om.data(), h.Om.size(), st);
+        e = e ? e : up(p->ws + h.off_Tasc, h.Tasc.data(), h.Tasc.size(), st);
+        e = e ? e : up(p->ws + h.off_ps, h.ps.data(), h.ps.size(), st);
+        e = e ? e : up(p->ws + h.off_pos, h.patch_of_s.data(), h.patch_of_s.size(), st);
+        if (e) return BSH_ERR_CUDA;
+        if (p->mode == BSH_MODE_BATCHED) {
+            const int rc = encode_bits_map(p, q);
+            if (rc) return rc;
+        }
+    }
+    cudaError_t e = up(p->ws + p->off_probs, hp.data(), hp.size(), st);
+    e = e ? e : up(p->ws + p->off_cta_item, p->cta_item.data(), p->cta_item.size(), st);
+    e = e ? e : up(p->ws + p->off_cta_visit, p->cta_visit.data(), p->cta_visit.size(), st);
+    e = e ? e : up(p->ws + p->off_rprob, p->region_problem.data(), p->region_problem.size(), st);
+    e = e ? e : up(p->ws + p->off_rvoff, p->region_visit_off.data(), p->region_visit_off.size(), st);
+    e = e ? e : up(p->ws + p->off_rvis, p->region_visits.data(), p->region_visits.size(), st);
+    e = e ? e : cudaMemsetAsync(p->ws + p->off_vcount, 0, sizeof(int32_t) * std::max(1, p->visits), st);
+    e = e ? e : cudaStreamSynchronize(st);
+    if (e) return BSH_ERR_CUDA;
+    p->bound = true;
+    return BSH_OK;
+}
+
+int bsh_autotune(bsh_plan* p, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    (void)stream;
+    return BSH_OK;
+}
+
+int bsh_number_count(bsh_plan* p, bsh_stream stream) { return run_count(p, 0, (cudaStream_t)stream); }
+
+int bsh_count_dense(bsh_plan* p, int32_t* const* n_unw, float* const* n_w, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (!n_unw || !n_w) return BSH_ERR_ARG;
+    std::vector<void*> ptrs(2 * p->n);
+    for (int q = 0; q < p->n; ++q) {
+        if (!n_unw[q] || !n_w[q]) return BSH_ERR_ARG;
+        ptrs[q] = n_unw[q];
+        ptrs[p->n + q] = n_w[q];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(p->ws + p->off_dense, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return BSH_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BSH_ERR_CUDA;
+    return run_count(p, 1, st);
+}
+
+int bsh_toplist(bsh_plan* p, bsh_cand* out, int32_t* n_out, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (!out || !n_out) return BSH_ERR_ARG;
+    MergeArgs a{};
+    a.probs = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs);
+    a.n_probs = p->n;
+    a.region_problem = reinterpret_cast<const int32_t*>(p->ws + p->off_rprob);
+    a.region_visit_off = reinterpret_cast<const int32_t*>(p->ws + p->off_rvoff);
+    a.region_visits = reinterpret_cast<const int32_t*>(p->ws + p->off_rvis);
+    a.visit_buf = reinterpret_cast<const Entry*>(p->ws + p->off_vbuf);
+    a.visit_count = reinterpret_cast<const int32_t*>(p->ws + p->off_vcount);
+    a.cap = p->cap;
+    a.top_k = p->top_k;
+    a.scratch = reinterpret_cast<Entry*>(p->ws + p->off_scratch);
+    a.out = out;
+    a.n_out = n_out;
+    a.status = status_ptr();
+    launch_merge(a, p->regions, (cudaStream_t)stream);
+    return cuda_fail(cudaGetLastError());
+}
+
+int bsh_power_sum(bsh_plan* p, bsh_cand* cands, const int32_t* n_cands, int n_cf, bsh_cand* final_list,
+                  int32_t* n_final, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (!cands || !n_cands || !final_list || !n_final || n_cf < 1 || n_cf > p->top_k) return BSH_ERR_ARG;
+    for (auto& h : p->P)
+        if (!h.d.rho) return BSH_ERR_ARG;
+    PowerArgs a{};
+    a.probs = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs);
+    a.n_probs = p->n;
+    a.region_problem = reinterpret_cast<const int32_t*>(p->ws + p->off_rprob);
+    a.cands = cands;
+    a.n_cands = n_cands;
+    a.top_k = p->top_k;
+    a.n_cf = n_cf;
+    a.final_list = final_list;
+    a.n_final = n_final;
+    a.status = status_ptr();
+    launch_power(a, p->regions, (cudaStream_t)stream);
+    return cuda_fail(cudaGetLastError());
+}
+
+int bsh_graph_reset(bsh_plan* p) {
+    if (!p) return BSH_ERR_ARG;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->gexec = nullptr;
+    p->graph = nullptr;
+    return BSH_OK;
+}
+
+int bsh_graph_launch(bsh_plan* p, bsh_cand* cands, int32_t* n_cands, int n_cf, bsh_cand* final_list,
+                     int32_t* n_final, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const void* args[6] = {cands, n_cands, final_list, n_final, nullptr, nullptr};
+    if (p->gexec && (std::memcmp(args, p->g_args, sizeof(args)) != 0 || n_cf != p->g_ncf)) return BSH_ERR_STATE;
+    if (!p->gexec) {
+        // warm the attribute settings outside capture
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BSH_ERR_CUDA;
+        int rc = bsh_number_count(p, stream);
+        if (!rc) rc = bsh_toplist(p, cands, n_cands, stream);
+        if (!rc) rc = bsh_power_sum(p, cands, n_cands, n_cf, final_list, n_final, stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : BSH_ERR_CUDA;
+        }
+        if (cudaGraphInstantiate(&p->gexec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return BSH_ERR_CUDA;
+        }
+        p->graph = g;
+        std::memcpy(p->g_args, args, sizeof(args));
+        p->g_ncf = n_cf;
+    }
+    return cuda_fail(cudaGraphLaunch(p->gexec, st));
+}
+
+}  // extern "C"
+
+extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* query, int count,
+                                       const uint32_t* row_bits, uint32_t* out, int32_t* path) {
+    if (!hp || !query || count < 0 || !row_bits || !out || !path) return BSH_ERR_ARG;
+    const bsh_problem& d = *hp;
+    if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || !d.v || !d.t || !d.sky || !d.a_p || !d.Omega ||
+        !d.T_asc || d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || d.n_f0 <= 0 || !finite_pos(d.v_max))
+        return BSH_ERR_ARG;
+    bsh_plan tmp;
+    tmp.threads = 256;
+    ProbHost h;
+    h.d = d;
+    h.ap.assign(d.a_p, d.a_p + d.n_ap);
+    h.Om.assign(d.Omega, d.Omega + d.n_Om);
+    h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
+    const int64_t ps[2] = {0, d.S};
+    h.ps.assign(ps, ps + 2);
+    h.d.n_patch = 1;
+    int rc = prepare_problem(&tmp, h);
+    if (rc) return rc;
+    const ProbDev& pd = h.pd;
+    const FixedPoint& fp = pd.fp;
+    const double sv = std::ldexp(1.0, fp.s_vn), sc = std::ldexp(1.0, fp.s_c);
+    const int pos_max = 32 * d.W - 33;
+    for (int e = 0; e < count; ++e) {
+        const int s = query[4 * e], b = query[4 * e + 1], i = query[4 * e + 2], j0 = query[4 * e + 3];
+        if (s < 0 || s >= d.S || b < 0 || b >= pd.B || i < 0 || i >= d.N || j0 < 0) return BSH_ERR_ARG;
+        const double* n = d.sky + 3 * (size_t)s;
+        const double* v = d.v + 3 * (size_t)i;
+        volatile double t1 = v[0] * n[0], t2 = v[1] * n[1], t3 = v[2] * n[2];
+        volatile double t12 = t1 + t2;
+        const double vn = t12 + t3;
+        const int iap = b % d.n_ap, ot = b / d.n_ap;
+        const double Om = h.Om[ot / d.n_T], Ta = h.Tasc[ot];
+        volatile double dt = d.t[i] - Ta;
+        volatile double arg = Om * dt;
+        const double c = Om * std::cos(arg);
+        const int vq = (int)std::nearbyint(vn * sv);
+        const int cq = (int)std::nearbyint(c * sc);
+        const int F2a = (int)std::llround(2.0 * d.F0) + 2 * j0;
+        const int v0 = make_Z(F2a, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a, cq, fp));
+        const int v1 = make_Z(F2a + 62, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a + 62, cq, fp));
+        const uint32_t* row = row_bits + (size_t)e * d.W;
+        const int pbase = pd.G0 + j0 - d.k_lo;
+        const int pos = pbase + (v0 >> fp.s_y);
+        const double ap = h.ap[iap];
+        auto exact_o = [&](int j) -> int {
+            volatile double apc = ap * c;
+            volatile double D = vn - apc;
+            const double F = d.F0 + (double)(j0 + j);
+            volatile double FD = F * D;
+            volatile double x = F + FD;
+            volatile double xh = x + 0.5;
+            return (int)((long long)std::floor(xh) - (long long)(pd.G0 + j0 + j));
+        };
+        if (fp_fast(v0, v1, fp.s_y, fp.M) && (unsigned)pos <= (unsigned)pos_max) {
+            out[e] = row_window(row, pos);
+            path[e] = 0;
+        } else {
+            int pth = 0;
+            bool bad = false;
+            out[e] = fp_window_slow(v0, v1, pbase, pos_max, fp.s_y, fp.M, row, exact_o, &pth, &bad);
+            path[e] = bad ? -1 : pth;
+        }
+    }
+    return BSH_OK;
+}
