@@ -267,6 +267,8 @@ struct CountArgs {
     int smem_bytes;
     int wseg_max, ot_max;
     int mode;                    // BSH_MODE_*
+    int max_n;                   // largest SFT count of the problems
+    int wrows;                   // Omega-T rows one warp needs at most
 };
 
 struct TmapSet {

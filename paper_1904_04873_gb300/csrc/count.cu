@@ -94,23 +94,30 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
     return r;
 }
 
-// Shared-memory layout of the batched kernel.
+// Shared-memory layout of the batched kernel: double-buffered TMA stages
+// (peakgram band, vn / weight / c table rows), per-warp track pairs, the
+// per-thread Kahan sums, stage barriers and arrival counters, and the
+// toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, cp, bar, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, cp, acc, comp, bar, done, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
 
-__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max) {
+__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads) {
     Layout L;
+    const int nw = threads / 32;
     int o = 0;
     for (int b = 0; b < 2; ++b) { L.pk[b] = o; o = align128(o + I * wseg * 4); }
     for (int b = 0; b < 2; ++b) { L.vn[b] = o; o = align128(o + I * 4); }
     for (int b = 0; b < 2; ++b) { L.w[b] = o; o = align128(o + I * 4); }
     for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + I * ot_max * 4); }
-    L.y = o; o = align128(o + I * 8);
-    L.cp = o; o = align128(o + I * ot_max * 8);
+    L.y = o; o = align128(o + nw * I * 8);
+    L.cp = o; o = align128(o + nw * I * wrows * 8);
+    L.acc = o; o = align128(o + JW * threads * 4);
+    L.comp = o; o = align128(o + JW * threads * 4);
     L.bar = o; o = align128(o + 16);
+    L.done = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
     L.misc = o; o = align128(o + 64);
     L.total = o;
@@ -122,6 +129,7 @@ struct TopSmem {
     int count;
     int have_tau;
     float mean, inv_sig;
+    int abort;
 };
 
 // Per-item constants shared by every thread.
@@ -290,16 +298,55 @@ __device__ void emit_item(const CountArgs& a, const ProbDev& P, const ItemCtx& c
 }
 
 // ------------------------------------------------------------ batched kernel
+// Kahan-compensated fold of the 64-SFT block sums into the per-thread sums
+// kept in shared memory (column `tid`, conflict-free).
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 1)
+__device__ __forceinline__ void kahan_fold(float* part, float* sacc, float* scomp, int tid) {
+#pragma unroll
+    for (int j = 0; j < JW; ++j) {
+        const float a0 = sacc[j * THREADS + tid];
+        const float c0 = scomp[j * THREADS + tid];
+        const float y = part[j] - c0;
+        const float t = a0 + y;
+        scomp[j * THREADS + tid] = (t - a0) - y;
+        sacc[j * THREADS + tid] = t;
+        part[j] = 0.f;
+    }
+}
+
+// Chunk `ch + ahead` of the item sequence starting at `it`: returns false past the CTA's range.
+__device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, int ch, int ahead, long long it_end,
+                                              int threads, ItemCtx* out, int* out_ch) {
+    ItemCtx c = item_ctx(a, decode_item(a, it), threads);
+    int k = ch + ahead;
+    while (k >= c.nchunks) {
+        k -= c.nchunks;
+        ++it;
+        if (it >= it_end) return false;
+        c = item_ctx(a, decode_item(a, it), threads);
+    }
+    *out = c;
+    *out_ch = k;
+    return true;
+}
+
+template <int THREADS, int NE>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS)
     count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max);
+    constexpr int NW = THREADS / 32;
+    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max, a.wrows, THREADS);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
+    unsigned* done = reinterpret_cast<unsigned*>(smem + L.done);
     SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem + L.sel);
     TopSmem& ts = *reinterpret_cast<TopSmem*>(smem + L.misc);
-    const int tid = threadIdx.x;
+    float* sacc = reinterpret_cast<float*>(smem + L.acc);
+    float* scomp = reinterpret_cast<float*>(smem + L.comp);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int I = a.chunk;
+    const int wrows = a.wrows;
+    int2* yp = reinterpret_cast<int2*>(smem + L.y) + warp * I;
+    int2* cp = reinterpret_cast<int2*>(smem + L.cp) + warp * I * wrows;
 
     long long it = a.cta_item[blockIdx.x];
     const long long it_end = a.cta_item[blockIdx.x + 1];
@@ -311,14 +358,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
+        done[0] = 0u;
+        done[1] = 0u;
         ts.count = 0;
         ts.have_tau = 0;
         ts.tau = 0ull;
+        ts.abort = 0;
     }
     __syncthreads();
 
     ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
-    if (tid == 0) issue_stage(a, maps, cur, 0, smem, L, 0);
+    if (tid == 0) {
+        issue_stage(a, maps, cur, 0, smem, L, 0);
+        ItemCtx nx;
+        int nch;
+        if (advance_chunk(a, it, 0, 1, it_end, THREADS, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1);
+    }
     unsigned g = 0;   // chunk sequence number within this CTA
 
     while (true) {
@@ -326,13 +381,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int b = cur.bt * THREADS + tid;
         const bool bvalid = b < P.B;
         const int iap = bvalid ? b % P.n_ap : 0;
-        const int ot = bvalid ? b / P.n_ap - cur.ot0 : 0;
+        const int b_w0 = cur.bt * THREADS + warp * 32;          // first binary of this warp
+        const int otw0 = imin(b_w0, P.B - 1) / P.n_ap;         // first Omega-T row of this warp
+        const int otw1 = imin(b_w0 + 31, P.B - 1) / P.n_ap;
+        const int nrw = otw1 - otw0 + 1;                        // rows this warp needs (<= wrows)
+        const int ot = bvalid ? b / P.n_ap - otw0 : 0;
+        const int orow0 = otw0 - cur.ot0;                       // their offset in the CTA's staged rows
         const int apq = bvalid ? P.ap_q[iap] : 0;
         const uint32_t jmask = bvalid ? (cur.jb >= 32 ? 0xffffffffu : ((1u << cur.jb) - 1u)) : 0u;
         const int s_y = P.fp.s_y, M = P.fp.M;
         const int wseg = a.wseg_max;
         const int pos_max = 32 * wseg - 33;
-        const int ot_max = a.ot_max;
+        const int pbase = cur.pbase;
 
         // new region -> new visit buffer
         if (!a.dense && cur.region != region) {
@@ -347,72 +407,81 @@ __global__ void __launch_bounds__(THREADS, 1)
             ts.inv_sig = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
         }
 
-        float part[JW], acc[JW], comp[JW];
+        float part[JW];
 #pragma unroll
-        for (int j = 0; j < JW; ++j) { part[j] = 0.f; acc[j] = 0.f; comp[j] = 0.f; }
+        for (int j = 0; j < JW; ++j) {
+            part[j] = 0.f;
+            sacc[j * THREADS + tid] = 0.f;
+            scomp[j * THREADS + tid] = 0.f;
+        }
         uint32_t ones = 0, twos = 0, fours = 0;
-        uint32_t e8[13];
+        uint32_t e8[NE];   // bit-sliced count of the 'eights' (N < 8 * 2^NE)
 #pragma unroll
-        for (int k = 0; k < 13; ++k) e8[k] = 0;
+        for (int k = 0; k < NE; ++k) e8[k] = 0;
 
         const int F2a = cur.F2a, F2b = cur.F2a + 62;
+        bool aborted = false;
         for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
             const int buf = g & 1;
-            const bool ok = mbar_wait(&bars[buf], (g >> 1) & 1);
-            if (__syncthreads_or(!ok)) {      // every thread leaves together
-                if (tid == 0) set_status(a.status, ST_TIMEOUT);
-                return;
+            if (!mbar_wait(&bars[buf], (g >> 1) & 1)) {
+                if (lane == 0) {
+                    set_status(a.status, ST_TIMEOUT);
+                    ts.abort = 1;
+                }
+                aborted = true;
+                break;
             }
-            // tables of this chunk: Z and C_q at j0 and j0 + 31
+            // this warp's track pairs for the chunk: Z and C_q at j0 and j0 + 31
             const int32_t* vnr = reinterpret_cast<const int32_t*>(smem + L.vn[buf]);
             const int32_t* cr = reinterpret_cast<const int32_t*>(smem + L.c[buf]);
-            int2* yp = reinterpret_cast<int2*>(smem + L.y);
-            int2* cp = reinterpret_cast<int2*>(smem + L.cp);
-            for (int e = tid; e < I; e += THREADS) {
+            for (int e = lane; e < I; e += 32) {
                 const int vq = vnr[e];
                 yp[e] = make_int2(make_Z(F2a, vq, P.fp), make_Z(F2b, vq, P.fp));
             }
-            for (int e = tid; e < I * cur.nrows; e += THREADS) {
+            for (int e = lane; e < I * nrw; e += 32) {
                 const int r = e / I, il = e - r * I;
-                const int cq = cr[e];
-                cp[il * ot_max + r] = make_int2(make_C(F2a, cq, P.fp), make_C(F2b, cq, P.fp));
+                const int cq = cr[(orow0 + r) * I + il];
+                cp[il * wrows + r] = make_int2(make_C(F2a, cq, P.fp), make_C(F2b, cq, P.fp));
             }
-            __syncthreads();
-            // prefetch the next chunk (or the next item's first chunk)
-            if (tid == 0) {
-                if (ch + 1 < cur.nchunks) {
-                    issue_stage(a, maps, cur, ch + 1, smem, L, buf ^ 1);
-                } else if (it + 1 < it_end) {
-                    const ItemCtx nx = item_ctx(a, decode_item(a, it + 1), THREADS);
-                    issue_stage(a, maps, nx, 0, smem, L, buf ^ 1);
-                }
-            }
+            __syncwarp();
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
             const float* wt = reinterpret_cast<const float*>(smem + L.w[buf]);
             const int i0 = ch * I;
-            const int nv = imin(I, P.N - i0);
             for (int g8 = 0; g8 < I; g8 += 8) {
                 uint32_t mk[8];
+                unsigned slow = 0u;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int il = g8 + u;
                     const int2 z = yp[il];
-                    const int2 cc = cp[il * ot_max + ot];
+                    const int2 cc = cp[il * wrows + ot];
                     const int v0 = z.x - __mulhi(apq, cc.x);
                     const int v1 = z.y - __mulhi(apq, cc.y);
-                    const int pos = cur.pbase + (v0 >> s_y);
-                    const uint32_t* row = pk + il * wseg;
-                    uint32_t m;
-                    if (fp_fast(v0, v1, s_y, M) && (unsigned)pos <= (unsigned)pos_max) {
-                        m = row_window(row, pos);
-                    } else if (il < nv && bvalid) {
-                        m = slow_window(P, v0, v1, cur.pbase, pos_max, row, cur.s, b, i0 + il, cur.j0, a.status);
-                    } else {
-                        m = 0u;
+                    const int pos = pbase + (v0 >> s_y);
+                    const bool fast = fp_fast(v0, v1, s_y, M) && (unsigned)pos <= (unsigned)pos_max;
+                    mk[u] = row_window(pk + il * wseg, fast ? pos : 0);
+                    slow |= (fast ? 0u : 1u) << u;
+                }
+                if (slow) {       // rare: boundary crossing or near-boundary terms
+#pragma unroll 1
+                    for (int u = 0; u < 8; ++u) {
+                        if (!((slow >> u) & 1u)) continue;
+                        const int il = g8 + u;
+                        const int2 z = yp[il];
+                        const int2 cc = cp[il * wrows + ot];
+                        const int v0 = z.x - __mulhi(apq, cc.x);
+                        const int v1 = z.y - __mulhi(apq, cc.y);
+                        mk[u] = (bvalid && i0 + il < P.N)
+                                    ? slow_window(P, v0, v1, pbase, pos_max, pk + il * wseg, cur.s, b, i0 + il,
+                                                  cur.j0, a.status)
+                                    : 0u;
                     }
-                    m = (il < nv) ? (m & jmask) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t m = mk[u] & jmask;
                     mk[u] = m;
-                    const float wv = wt[il];
+                    const float wv = wt[g8 + u];
 #pragma unroll
                     for (int j = 0; j < JW; ++j)
                         if (m & (1u << j)) part[j] += wv;
@@ -426,39 +495,40 @@ __global__ void __launch_bounds__(THREADS, 1)
                 csa(fB, twos, twos, tA, tB);
                 csa(eights, fours, fours, fA, fB);
 #pragma unroll
-                for (int k = 0; k < 13; ++k) {
+                for (int k = 0; k < NE; ++k) {
                     const uint32_t t = e8[k] & eights;
                     e8[k] ^= eights;
                     eights = t;
                 }
-                if ((g8 & 31) == 24) {   // every 32 SFTs: fold the block sums into the Kahan sums
-#pragma unroll
-                    for (int j = 0; j < JW; ++j) {
-                        const float y = part[j] - comp[j];
-                        const float t = acc[j] + y;
-                        comp[j] = (t - acc[j]) - y;
-                        acc[j] = t;
-                        part[j] = 0.f;
-                    }
+                if ((g8 & 63) == 56) kahan_fold<THREADS>(part, sacc, scomp, tid);   // every 64 SFTs
+            }
+            // done with this buffer: the last warp to finish refills it two chunks ahead
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();   // this warp's reads of the buffer precede its arrival
+                const unsigned prev = atomicAdd(&done[buf], 1u);
+                if (prev == NW * ((g >> 1) + 1) - 1) {
+                    ItemCtx nx;
+                    int nch;
+                    if (advance_chunk(a, it, ch, 2, it_end, THREADS, &nx, &nch))
+                        issue_stage(a, maps, nx, nch, smem, L, buf);
                 }
             }
-            __syncthreads();
         }
-        // fold the last partial block
+        // fold the last partial block and read out the counts
+        kahan_fold<THREADS>(part, sacc, scomp, tid);
         float nw[JW];
         uint32_t nu[JW];
 #pragma unroll
         for (int j = 0; j < JW; ++j) {
-            const float y = part[j] - comp[j];
-            const float t = acc[j] + y;
-            const float cpn = (t - acc[j]) - y;
-            nw[j] = t - cpn;
+            nw[j] = sacc[j * THREADS + tid] - scomp[j * THREADS + tid];
             uint32_t cnt = ((ones >> j) & 1u) + 2u * ((twos >> j) & 1u) + 4u * ((fours >> j) & 1u);
 #pragma unroll
-            for (int k = 0; k < 13; ++k) cnt += ((e8[k] >> j) & 1u) << (3 + k);
+            for (int k = 0; k < NE; ++k) cnt += ((e8[k] >> j) & 1u) << (3 + k);
             nu[j] = cnt;
         }
-        __syncthreads();   // ts.mean / ts.inv_sig visible
+        (void)aborted;
+        if (__syncthreads_or(ts.abort)) return;   // a wait expired somewhere: leave together
         emit_item<THREADS>(a, P, cur, b, bvalid, nw, nu, visit, ts, sm);
 
         ++it;
@@ -548,9 +618,9 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
 
 }  // namespace
 
-int count_smem_bytes(int mode, int I, int wseg, int ot_max) {
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads) {
     if (mode == BSH_MODE_PLAIN) return align128((int)sizeof(SelectSmem)) + align128((int)sizeof(TopSmem));
-    return make_layout(I, wseg, ot_max).total;
+    return make_layout(I, wseg, ot_max, wrows, threads).total;
 }
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st) {
@@ -567,14 +637,27 @@ void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads
         }
         return;
     }
+    const bool small_n = a.max_n < 8 * 1024;
     if (threads == 128) {
-        static int s_count_batched128 = 0;
-            ensure_smem(count_batched<128>, a.smem_bytes, &s_count_batched128);
-        count_batched<128><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+        if (small_n) {
+            static int s_b128_10 = 0;
+            ensure_smem(count_batched<128, 10>, a.smem_bytes, &s_b128_10);
+            count_batched<128, 10><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+        } else {
+            static int s_b128_13 = 0;
+            ensure_smem(count_batched<128, 13>, a.smem_bytes, &s_b128_13);
+            count_batched<128, 13><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+        }
     } else {
-        static int s_count_batched256 = 0;
-            ensure_smem(count_batched<256>, a.smem_bytes, &s_count_batched256);
-        count_batched<256><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+        if (small_n) {
+            static int s_b256_10 = 0;
+            ensure_smem(count_batched<256, 10>, a.smem_bytes, &s_b256_10);
+            count_batched<256, 10><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+        } else {
+            static int s_b256_13 = 0;
+            ensure_smem(count_batched<256, 13>, a.smem_bytes, &s_b256_13);
+            count_batched<256, 13><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+        }
     }
 }
 

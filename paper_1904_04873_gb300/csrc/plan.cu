@@ -13,7 +13,7 @@
 #include "bsh_internal.cuh"
 
 namespace bsh {
-int count_smem_bytes(int mode, int I, int wseg, int ot_max);
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads);
 }
 
 using namespace bsh;
@@ -99,7 +99,7 @@ struct bsh_plan {
     bsh_count_options opt{};
     int mode = BSH_MODE_BATCHED;
     int threads = 256, chunk = 128, ctas = 0, num_sms = 152;
-    int wseg_max = 4, ot_max = 1, smem = 0, cap = 0, top_k = 1000;
+    int wseg_max = 4, ot_max = 1, wrows = 1, smem = 0, cap = 0, top_k = 1000;
     int regions = 0, visits = 0;
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
@@ -115,6 +115,7 @@ struct bsh_plan {
     // graph
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
     const void* g_args[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int g_ncf = 0;
 };
@@ -327,6 +328,7 @@ void bsh_plan_destroy(bsh_plan* p) {
     if (!p) return;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
 }
 
@@ -344,9 +346,12 @@ namespace {
 int build_schedule(bsh_plan* p) {
     // tile shapes
     p->ot_max = 1;
+    p->wrows = 1;
     for (auto& h : p->P) {
         const int rows = std::min(h.d.n_Om * h.d.n_T, (p->threads + h.d.n_ap - 1) / h.d.n_ap + 1);
         p->ot_max = std::max(p->ot_max, rows);
+        const int wr = std::min(h.d.n_Om * h.d.n_T, (32 + h.d.n_ap - 1) / h.d.n_ap + 1);
+        p->wrows = std::max(p->wrows, wr);
     }
     int region = 0;
     long long items = 0;
@@ -359,12 +364,23 @@ int build_schedule(bsh_plan* p) {
     }
     p->regions = region;
     // chunk size: shrink until the shared-memory layout fits
+    // chunk size: shrink until two CTAs fit one SM's shared memory (else one)
+    const int smem_two = 112 * 1024, smem_one = 220 * 1024;
+    const int chunk0 = p->chunk;
     while (true) {
-        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max);
-        if (p->smem <= 220 * 1024 || p->chunk <= 32) break;
+        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads);
+        if (p->smem <= smem_two || p->chunk <= 32) break;
         p->chunk /= 2;
     }
-    if (p->smem > 220 * 1024) return BSH_ERR_RANGE;
+    if (p->smem > smem_two) {
+        p->chunk = chunk0;
+        while (true) {
+            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads);
+            if (p->smem <= smem_one || p->chunk <= 32) break;
+            p->chunk /= 2;
+        }
+    }
+    if (p->smem > smem_one) return BSH_ERR_RANGE;
     std::vector<long long> cum_cost(p->n + 1, 0);
     for (int q = 0; q < p->n; ++q) {
         ProbDev& pd = p->P[q].pd;
@@ -376,7 +392,8 @@ int build_schedule(bsh_plan* p) {
         cum_cost[q + 1] = cum_cost[q] + pd.n_items * pd.cost;
     }
     const long long total_items = items;
-    const int cps = p->opt.ctas_per_sm ? p->opt.ctas_per_sm : 1;
+    const int cps = p->opt.ctas_per_sm ? p->opt.ctas_per_sm
+                    : (p->mode == BSH_MODE_BATCHED && p->smem <= smem_two ? 512 / p->threads : 1);
     const int k = p->top_k;
     // region item ranges
     std::vector<long long> r_begin(p->regions + 1, 0);
@@ -538,6 +555,9 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.wseg_max = p->wseg_max;
     a.ot_max = p->ot_max;
     a.mode = p->mode;
+    a.wrows = p->wrows;
+    a.max_n = 0;
+    for (auto& h : p->P) a.max_n = std::max(a.max_n, h.d.N);
     return a;
 }
 
@@ -711,13 +731,18 @@ int bsh_graph_launch(bsh_plan* p, bsh_cand* cands, int32_t* n_cands, int n_cf, b
     const void* args[6] = {cands, n_cands, final_list, n_final, nullptr, nullptr};
     if (p->gexec && (std::memcmp(args, p->g_args, sizeof(args)) != 0 || n_cf != p->g_ncf)) return BSH_ERR_STATE;
     if (!p->gexec) {
-        // warm the attribute settings outside capture
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BSH_ERR_CUDA;
-        int rc = bsh_number_count(p, stream);
-        if (!rc) rc = bsh_toplist(p, cands, n_cands, stream);
-        if (!rc) rc = bsh_power_sum(p, cands, n_cands, n_cf, final_list, n_final, stream);
+        // Record on a private stream: the caller's stream may be the legacy
+        // default stream, which cannot be captured.  The graph is then
+        // launched on the caller's stream.
+        if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return BSH_ERR_CUDA;
+        cudaStream_t cs = p->cap_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BSH_ERR_CUDA;
+        int rc = bsh_number_count(p, (bsh_stream)cs);
+        if (!rc) rc = bsh_toplist(p, cands, n_cands, (bsh_stream)cs);
+        if (!rc) rc = bsh_power_sum(p, cands, n_cands, n_cf, final_list, n_final, (bsh_stream)cs);
         cudaGraph_t g = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (rc || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return rc ? rc : BSH_ERR_CUDA;

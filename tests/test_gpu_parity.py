@@ -66,7 +66,9 @@ def test_weights(dtype):
     ow = oracle.weights(pr.sky, pr.arms, pr.Sn, norm=True)
     gw = w.double().cpu().numpy()
     if dtype == "f64":
-        assert np.allclose(gw, ow, rtol=1e-12, atol=0)
+        # F+^2 + Fx^2 is formed differently on the two sides; near antenna nulls the
+        # difference is absolute (weights are normalised to mean 1)
+        assert np.allclose(gw, ow, rtol=1e-12, atol=1e-12)
     else:
         oq = oracle.quantize(ow, dtype)
         ulp = {"f32": 2.0 ** -23, "f16": 2.0 ** -10, "bf16": 2.0 ** -7}[dtype]
