@@ -10,7 +10,8 @@
  *   - Array arguments are DEVICE pointers owned by the caller unless the
  *     comment says HOST.  The library never allocates device memory: the
  *     only device memory it uses besides the caller's arrays is the plan
- *     workspace the caller passes to bsh_plan_bind().
+ *     workspace the caller passes to bsh_plan_bind(), and the fixed-size
+ *     static array behind bsh_power_sum_static().
  *   - Calls taking a stream only enqueue work on it (asynchronous).  Those
  *     marked "capturable" make no host synchronisation and no allocation and
  *     may be recorded into a CUDA graph.
@@ -248,6 +249,33 @@ int bsh_graph_reset(bsh_plan* plan);
 /* ------------------------------------------------------------------------ */
 int bsh_debug_track_windows(const bsh_problem* host_problem, const int32_t* query /*[count][4]: s,b,i,j0*/,
                             int count, const uint32_t* row_bits, uint32_t* out, int32_t* path);
+
+/* ------------------------------------------------------------------------ */
+/* Stage-2 power sum that allocates nothing.  The paper has no counterpart:  */
+/* this entry point exists for callers that cannot allocate device memory   */
+/* (for example code running where cudaMalloc is forbidden or unavailable,  */
+/* such as inside a host callback, a memory-pool-less embedding, or a        */
+/* process whose allocator is owned by another runtime).  It needs no plan  */
+/* and no workspace: its scratch (the FP64 / fixed-point track tables and   */
+/* weights of one problem) lives in one static device array of              */
+/* BSH_STATIC_SCRATCH_BYTES that every GPU loading this library keeps until */
+/* process exit.                                                              */
+/*                                                                          */
+/* problem: as for bsh_plan_create (HOST grid and patch arrays, DEVICE data */
+/*   arrays, rho required).  template_ids [n] DEVICE int64:                  */
+/*   template ids ((s * B + b) * n_f0 + j).  power, s_p [n] DEVICE float:     */
+/*   P and s_P of Eq. (26) for each id, the same values bsh_power_sum gives. */
+/* Returns BSH_ERR_WORKSPACE when the problem's tables exceed the static     */
+/* array (S * N' * 8 + n_Om * n_T * N' * 12 bytes plus the grids, with N'   */
+/* = N rounded up to 256).  The first call on a device looks up the array's */
+/* device address (make that first call before any stream capture).  Every  */
+/* call overwrites the whole array, so calls that overlap on the GPU (other */
+/* streams, other threads) race and must be serialised by the caller.       */
+/* Kernel-side errors are reported by bsh_sync_status.                      */
+/* ------------------------------------------------------------------------ */
+#define BSH_STATIC_SCRATCH_BYTES (32u << 20)
+int bsh_power_sum_static(const bsh_problem* problem, const int64_t* template_ids, int n, float* power,
+                         float* s_p, bsh_stream stream);
 
 #ifdef __cplusplus
 }

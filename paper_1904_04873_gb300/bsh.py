@@ -88,6 +88,8 @@ _SIGS = {
     "bsh_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_graph_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_power_sum_static": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -297,6 +299,20 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def power_sum_static(dp: "DeviceProblem", template_ids, stream=None):
+    """bsh_power_sum_static: P and s_P for a device int64 list of template ids,
+    with the library's static scratch instead of a plan workspace."""
+    import torch
+    ids = template_ids.contiguous()
+    n = ids.numel()
+    power = torch.empty(n, dtype=torch.float32, device=ids.device)
+    s_p = torch.empty(n, dtype=torch.float32, device=ids.device)
+    d = dp.descriptor()
+    _check(lib().bsh_power_sum_static(ctypes.byref(d), _ptr(ids), n, _ptr(power), _ptr(s_p), _stream(stream)),
+           "bsh_power_sum_static")
+    return power, s_p
 
 
 def cands_to_numpy(cands, n) -> List[np.ndarray]:

@@ -826,3 +826,187 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
     }
     return BSH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Power sum without allocation: scratch in a static device array.
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[BSH_STATIC_SCRATCH_BYTES];
+
+// Device address of g_static_scratch on the current device, looked up once per device.
+unsigned char* static_scratch_ptr() {
+    static std::mutex mu;
+    static unsigned char* ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<unsigned char*>(p);
+    }
+    return ptrs[dev];
+}
+
+__global__ void static_ap_q(const ProbDev* probs) {
+    const ProbDev& P = probs[0];
+    const double sc = ldexp(1.0, P.fp.s_a);
+    for (int k = threadIdx.x; k < P.n_ap; k += blockDim.x)
+        const_cast<int32_t*>(P.ap_q)[k] = (int32_t)llrint(P.a_p[k] * sc);
+}
+
+// One warp per listed template: Eq. (26) along the track, as in the plan's power kernel.
+__global__ void power_list_kernel(const ProbDev* probs, const int64_t* ids, int n, float* power, float* s_p,
+                                  unsigned* status) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= n) return;
+    const ProbDev& P = probs[0];
+    const long long id = ids[e];
+    const long long per_s = (long long)P.B * P.n_f0;
+    if (id < 0 || id >= per_s * P.S) {
+        if (lane == 0) {
+            set_status(status, ST_ARG);
+            power[e] = 0.f;
+            s_p[e] = 0.f;
+        }
+        return;
+    }
+    const int s = (int)(id / per_s);
+    const long long rem = id % per_s;
+    const int b = (int)(rem / P.n_f0);
+    const int j = (int)(rem % P.n_f0);
+    const double F = P.F0 + (double)j;
+    const int F2 = (int)llrint(2.0 * F);
+    const int G = P.G0 + j;
+    const int iap = b % P.n_ap, ot = b / P.n_ap;
+    const int apq = P.ap_q[iap];
+    const double ap = P.a_p[iap];
+    const int s_y = P.fp.s_y, M = P.fp.M;
+    const int cell = 1 << s_y;
+    const double* nv = P.sky + 3 * (size_t)s;
+    float sum = 0.f, comp = 0.f;
+    for (int i = lane; i < P.N; i += 32) {
+        const int Z = make_Z(F2, P.vn_q[(size_t)s * P.Np + i], P.fp);
+        const int C = make_C(F2, P.c_q[(size_t)ot * P.Np + i], P.fp);
+        const int v = Z - mulhi32(apq, C);
+        const int fr = v & (cell - 1);
+        int o = v >> s_y;
+        if (fr < M || fr > cell - M) {
+            const double* vv = P.v + 3 * (size_t)i;
+            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(vv[0], nv[0]), __dmul_rn(vv[1], nv[1])),
+                                        __dmul_rn(vv[2], nv[2]));
+            const double D = __dsub_rn(vn, __dmul_rn(ap, P.c64[(size_t)ot * P.Np + i]));
+            const double x = __dadd_rn(F, __dmul_rn(F, D));
+            o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)G);
+        }
+        const int col = G + o - P.k_lo;
+        if (col < 0 || col >= P.K) {
+            set_status(status, ST_RANGE);
+            continue;
+        }
+        const float x = P.w32[(size_t)s * P.Np + i] * __ldg(P.rho + (size_t)i * P.K + col);
+        const float y = x - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    float v = sum - comp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+        const double sw = P.sum_w[s], sw2 = P.sum_w2[s];
+        power[e] = v;
+        s_p[e] = sw2 > 0.0 ? (float)(((double)v - sw) / sqrt(sw2)) : 0.f;
+    }
+}
+
+}  // namespace
+
+extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* template_ids, int n, float* power,
+                                    float* s_p, bsh_stream stream) {
+    if (!problem || n < 0 || (n > 0 && (!template_ids || !power || !s_p))) return BSH_ERR_ARG;
+    const bsh_problem& d = *problem;
+    int rc = validate_problem(d);
+    if (rc) return rc;
+    if (!d.rho) return BSH_ERR_ARG;
+    if (n == 0) return BSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbDev pd;
+    std::memset(&pd, 0, sizeof(pd));
+    pd.N = d.N;
+    pd.Np = (d.N + 255) / 256 * 256;
+    pd.K = d.K;
+    pd.W = d.W;
+    pd.k_lo = d.k_lo;
+    pd.n_f0 = d.n_f0;
+    pd.S = d.S;
+    pd.n_ap = d.n_ap;
+    pd.n_Om = d.n_Om;
+    pd.n_T = d.n_T;
+    pd.nOT = d.n_Om * d.n_T;
+    const long long B = (long long)d.n_ap * pd.nOT;
+    if (B > (1LL << 30) || (double)B * d.n_f0 * d.S > 9.0e18) return BSH_ERR_RANGE;
+    pd.B = (int)B;
+    pd.w_dtype = d.w_dtype;
+    pd.F0 = d.F0;
+    pd.G0 = (int)std::floor(d.F0);
+    pd.p_th = std::exp(-d.rho_th);
+    pd.v_max = d.v_max;
+    double ap_max = 0.0, Om_max = 0.0;
+    for (int k = 0; k < d.n_ap; ++k) ap_max = std::max(ap_max, d.a_p[k]);
+    for (int k = 0; k < d.n_Om; ++k) Om_max = std::max(Om_max, d.Omega[k]);
+    // the same fixed-point scales as a plan of this problem
+    const int nb = (d.n_f0 + JW - 1) / JW;
+    const int JB = (d.n_f0 + nb - 1) / nb;
+    const int n_fb = (d.n_f0 + JB - 1) / JB;
+    const double F_eval = d.F0 + (n_fb - 1) * JB + JW;
+    rc = choose_fixed_point(F_eval, d.v_max, ap_max, Om_max, d.F0 - std::floor(d.F0), &pd.fp);
+    if (rc) return rc;
+    const double Fv_max = d.F0 + d.n_f0 - 1;
+    const double yv = Fv_max * (d.v_max + ap_max * Om_max);
+    const long long kmin = (long long)std::floor(d.F0 - yv + 0.5) - 1;
+    const long long kmax = (long long)std::floor(Fv_max + yv + 0.5) + 1;
+    if (kmin < d.k_lo || kmax >= (long long)d.k_lo + d.K) return BSH_ERR_RANGE;
+    // scratch layout inside the static array
+    size_t o = 0;
+    const size_t off_pd = o; o = al(o + sizeof(ProbDev));
+    const size_t off_ap = o; o = al(o + sizeof(double) * d.n_ap);
+    const size_t off_apq = o; o = al(o + sizeof(int32_t) * d.n_ap);
+    const size_t off_Om = o; o = al(o + sizeof(double) * d.n_Om);
+    const size_t off_Ta = o; o = al(o + sizeof(double) * pd.nOT);
+    const size_t off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)d.S * pd.Np);
+    const size_t off_w = o; o = al(o + sizeof(float) * (size_t)d.S * pd.Np);
+    const size_t off_cq = o; o = al(o + sizeof(int32_t) * (size_t)pd.nOT * pd.Np);
+    const size_t off_c64 = o; o = al(o + sizeof(double) * (size_t)pd.nOT * pd.Np);
+    if (o > (size_t)BSH_STATIC_SCRATCH_BYTES) return BSH_ERR_WORKSPACE;
+    unsigned char* base = static_scratch_ptr();
+    unsigned* sp = status_ptr();
+    if (!base || !sp) return BSH_ERR_CUDA;
+    pd.bits = d.bits;
+    pd.rho = d.rho;
+    pd.w = d.w;
+    pd.sum_w = d.sum_w;
+    pd.sum_w2 = d.sum_w2;
+    pd.v = d.v;
+    pd.t = d.t;
+    pd.sky = d.sky;
+    pd.a_p = reinterpret_cast<const double*>(base + off_ap);
+    pd.ap_q = reinterpret_cast<const int32_t*>(base + off_apq);
+    pd.Om = reinterpret_cast<const double*>(base + off_Om);
+    pd.Tasc = reinterpret_cast<const double*>(base + off_Ta);
+    pd.vn_q = reinterpret_cast<int32_t*>(base + off_vnq);
+    pd.w32 = reinterpret_cast<float*>(base + off_w);
+    pd.c_q = reinterpret_cast<int32_t*>(base + off_cq);
+    pd.c64 = reinterpret_cast<double*>(base + off_c64);
+    cudaError_t e = cudaMemcpyAsync(base + off_pd, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(base + off_ap, d.a_p, sizeof(double) * d.n_ap, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(base + off_Om, d.Omega, sizeof(double) * d.n_Om, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(base + off_Ta, d.T_asc, sizeof(double) * pd.nOT, cudaMemcpyHostToDevice, st);
+    if (e) return BSH_ERR_CUDA;
+    const ProbDev* dpd = reinterpret_cast<const ProbDev*>(base + off_pd);
+    static_ap_q<<<1, 256, 0, st>>>(dpd);
+    launch_tables(pd, dpd, BSH_MODE_BATCHED, sp, st);
+    const int warps = 8;
+    power_list_kernel<<<(n + warps - 1) / warps, warps * 32, 0, st>>>(dpd, template_ids, n, power, s_p, sp);
+    return cuda_fail(cudaGetLastError());
+}

@@ -1,0 +1,78 @@
+"""bsh_power_sum_static against bsh_power_sum, through the C ABI.
+
+bsh_power_sum_static is for callers that cannot allocate device memory (no
+cudaMalloc and no caching allocator available where they run): it needs no
+plan and no workspace and keeps its track tables in a fixed-size static
+device array inside the library.  Its P and s_P must match the plan-based
+power sum of the same candidates within the stage-2 tolerance, on two calls
+in a row (the second call reuses, and must fully rewrite, the static array).
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_1904_04873_gb300 import bsh
+from _common import small_mid
+from gpu_common import REL_TOL, device_problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1904_04873_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _reference(dp, top_k):
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=top_k)
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(min(8, top_k))
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    plan.close()
+    return np.concatenate(lists)
+
+
+def _check(dp, ref):
+    ids = torch.as_tensor(ref["template_id"], dtype=torch.int64, device="cuda")
+    power, s_p = bsh.power_sum_static(dp, ids)
+    assert bsh.sync_status() == bsh.OK
+    power = power.cpu().numpy()
+    s_p = s_p.cpu().numpy()
+    P = ref["power"].astype(np.float64)
+    assert np.all(np.abs(power - P) <= REL_TOL * np.abs(P))
+    assert np.all(np.abs(s_p - ref["s_p"]) < 1e-4)
+
+
+def test_static_power_sum_matches_plan_twice():
+    pr1 = small_mid(n_sky=6, n_per_det=150, n_ap=4, n_P=3, n_T=3, patch_size=3, top_k=30)
+    pr2 = small_mid(n_sky=9, n_per_det=100, n_ap=8, n_P=2, n_T=4, patch_size=3, top_k=20, seed=77)
+    dp1, _, _ = device_problem(pr1, "f16")
+    dp2, _, _ = device_problem(pr2, "f32")
+    ref1 = _reference(dp1, 30)
+    ref2 = _reference(dp2, 20)
+    _check(dp1, ref1)      # first call on this device sets up the static scratch
+    _check(dp2, ref2)      # second call, different problem: the array is rewritten
+    _check(dp1, ref1)
+
+
+def test_static_power_sum_rejects_oversized_problem():
+    pr = small_mid(n_sky=2, n_per_det=64, n_ap=2, n_P=2, n_T=2, patch_size=2, top_k=5)
+    dp, _, _ = device_problem(pr, "f16")
+    d = dp.descriptor()
+    # 2 x 6000 Omega-T rows of 256 SFTs need 12000 x 256 x 12 bytes > 32 MiB of tables
+    big_T = np.ascontiguousarray(np.tile(pr.T_asc, (1, 3000)))
+    d.n_T = big_T.shape[1]
+    d.T_asc = big_T.ctypes.data
+    ids = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = torch.empty(1, dtype=torch.float32, device="cuda")
+    rc = bsh.lib().bsh_power_sum_static(d, ids.data_ptr(), 1, out.data_ptr(), out.data_ptr(),
+                                        bsh._stream())
+    assert rc == bsh.ERR_WORKSPACE
