@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
     return ap.parse_args()
 
 
@@ -123,6 +124,29 @@ class ClockSampler:
             out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                    "samples": len(sm)}
         return out
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per count launch from the committed ncu summary, if it was taken
+    on the current kernel sources (same short hash) and on this workload."""
+    import hashlib
+    if kind != "mid":
+        return None, None
+    src = os.path.join(ROOT, "paper_1904_04873_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
+        h.update(open(os.path.join(src, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "count_batched_mid.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, None
+    vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_launch:",
+                                                                          "kernel_source_sha256_16:")))
+    if vals.get("kernel_source_sha256_16", "").strip() != sha:
+        return None, "profiles/count_batched_mid.md (stale: kernel changed since)"
+    return float(vals["traffic_bytes_per_launch"]), "profiles/count_batched_mid.md"
 
 
 def measured_peaks():
@@ -218,6 +242,8 @@ def main():
     dp = bsh.DeviceProblem(pr, w_dtype="f16")
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=args.threads, sft_chunk=args.chunk)
     n_cf = 100
+    dp.prepare()
+    tile = plan.tile() if args.no_tune else plan.autotune()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -349,14 +375,19 @@ def main():
     count_rate = pr.n_terms / count_s
     achieved_gbs = count_rate * 4.0 / 1e9
     peak_gbs = n_sm * 128.0 * f_max / 1e9
+    traffic, traffic_src = profiled_traffic(args.workload)
     roofline = {"bound": "smem", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                "frac": achieved_gbs / peak_gbs, "traffic": None,
+                "frac": achieved_gbs / peak_gbs, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "bsh_number_count (track tables + count_batched)",
                 "peak_source": f"derived: {n_sm} SMs x 32 banks x 4 B/clk x {f_max / 1e6:.0f} MHz "
                                f"(MEASURED_PEAKS sm_max_mhz); one 32-bit word per term",
                 "terms_per_s": count_rate, "count_ms": count_s * 1e3}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
+    # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the
+    # 3.7 thread instructions per term measured by ncu (profiles/count_batched_small_full.md)
+    roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / 3.7, "instr_per_term": 3.7,
+                       "frac": count_rate / (n_sm * 128.0 * f_max / 3.7)}
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -368,7 +399,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
                 "config": workload_config(pr, args.workload) | {"parallelism": f"replicas x{world}",
-                                                                  "graph": bool(args.graph)},
+                                                                  "graph": bool(args.graph), "tile": tile},
                 "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
                 "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline,
                 "plain": plain, "cpu_baseline": cpu}

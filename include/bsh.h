@@ -180,9 +180,15 @@ int bsh_plan_first_region(const bsh_plan* plan, int problem);
  * stream-ordered copies; synchronises `stream`.  Not capturable; call once. */
 int bsh_plan_bind(bsh_plan* plan, void* workspace, size_t bytes, bsh_stream stream);
 
-/* Runs the autotuner: times the candidate tile shapes on a slice of the work
- * list and keeps the fastest.  Synchronises; not capturable. */
+/* Runs the autotuner: times the candidate tile shapes (CTA size 256 or 128
+ * binary templates, 64 / 128 / 256 SFTs per shared-memory stage, unless fixed
+ * by the options) on a slice of the work list of about six items per CTA,
+ * keeps the fastest and re-uploads the plan.  Synchronises; not capturable;
+ * drops a recorded graph. */
 int bsh_autotune(bsh_plan* plan, bsh_stream stream);
+
+/* Current tile shape: CTA size, SFTs per stage, persistent CTAs in the grid. */
+int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas);
 
 /* ------------------------------------------------------------------------ */
 /* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */

@@ -80,6 +80,8 @@ _SIGS = {
     "bsh_plan_first_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bsh_plan_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "bsh_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_plan_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
     "bsh_number_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_count_dense": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_toplist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -288,6 +290,12 @@ class Plan:
 
     def autotune(self, stream=None):
         _check(lib().bsh_autotune(self.h, _stream(stream)), "bsh_autotune")
+        return self.tile()
+
+    def tile(self):
+        t, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bsh_plan_tile(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g)), "bsh_plan_tile")
+        return {"threads": t.value, "sft_chunk": c.value, "ctas": g.value}
 
     def close(self):
         if self.h:

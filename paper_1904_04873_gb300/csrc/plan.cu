@@ -100,7 +100,9 @@ struct bsh_plan {
     int mode = BSH_MODE_BATCHED;
     int threads = 256, chunk = 128, ctas = 0, num_sms = 152;
     int wseg_max = 4, ot_max = 1, wrows = 1, smem = 0, cap = 0, top_k = 1000;
-    int regions = 0, visits = 0;
+    int regions = 0, visits = 0, visit_cap = 0;
+    size_t ws_cap = 0;                     // workspace bytes: the largest of the tuning candidates
+    double tuned_rate = 0.0;
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
@@ -124,7 +126,20 @@ namespace {
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-int build_schedule(bsh_plan* p);
+// Tile shapes the autotuner considers (the first is the default).
+std::vector<int> tune_threads(const bsh_plan* p) {
+    if (p->opt.threads) return {p->opt.threads};
+    if (p->mode == BSH_MODE_PLAIN) return {256};
+    return {256, 128};
+}
+std::vector<int> tune_chunks(const bsh_plan* p) {
+    if (p->opt.sft_chunk) return {p->opt.sft_chunk};
+    if (p->mode == BSH_MODE_PLAIN) return {128};
+    return {128, 64, 256};
+}
+
+int build_schedule(bsh_plan* p, long long item_limit = -1);
+int upload_plan(bsh_plan* p, cudaStream_t st);
 
 int validate_problem(const bsh_problem& d) {
     if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || d.W % 4 != 0) return BSH_ERR_ARG;
@@ -315,11 +330,25 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
         h.d.T_asc = nullptr;
         h.d.patch_start = nullptr;
     }
+    // size the workspace for every tile shape the autotuner may pick
+    size_t cap = 0;
+    int first_rc = -1;
+    for (int t : tune_threads(p))
+        for (int c : tune_chunks(p)) {
+            p->threads = t;
+            p->chunk = c;
+            const int rc = build_schedule(p);
+            if (first_rc < 0) first_rc = rc;
+            if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
+        }
+    p->threads = tune_threads(p)[0];
+    p->chunk = tune_chunks(p)[0];
     const int rc = build_schedule(p);
     if (rc) {
         delete p;
         return rc;
     }
+    p->ws_cap = std::max(cap, p->ws_size);
     *out = p;
     return BSH_OK;
 }
@@ -332,7 +361,7 @@ void bsh_plan_destroy(bsh_plan* p) {
     delete p;
 }
 
-size_t bsh_plan_workspace_size(const bsh_plan* p) { return p ? p->ws_size : 0; }
+size_t bsh_plan_workspace_size(const bsh_plan* p) { return p ? p->ws_cap : 0; }
 int bsh_plan_num_regions(const bsh_plan* p) { return p ? p->regions : 0; }
 int bsh_plan_first_region(const bsh_plan* p, int q) {
     if (!p || q < 0 || q >= p->n) return -1;
@@ -343,7 +372,7 @@ int bsh_plan_first_region(const bsh_plan* p, int q) {
 
 namespace {
 
-int build_schedule(bsh_plan* p) {
+int build_schedule(bsh_plan* p, long long item_limit) {
     // tile shapes
     p->ot_max = 1;
     p->wrows = 1;
@@ -363,9 +392,10 @@ int build_schedule(bsh_plan* p) {
         p->wseg_max = std::max(p->wseg_max, h.pd.Wseg);
     }
     p->regions = region;
-    // chunk size: shrink until the shared-memory layout fits
-    // chunk size: shrink until two CTAs fit one SM's shared memory (else one)
-    const int smem_two = 112 * 1024, smem_one = 220 * 1024;
+    // chunk size: shrink until the CTAs that the register budget allows per SM
+    // (512 threads) also fit its shared memory; else settle for one CTA per SM
+    const int blocks_target = 512 / p->threads;
+    const int smem_two = (227 * 1024) / blocks_target - 1024, smem_one = 220 * 1024;
     const int chunk0 = p->chunk;
     while (true) {
         p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads);
@@ -391,9 +421,10 @@ int build_schedule(bsh_plan* p) {
         items += pd.n_items;
         cum_cost[q + 1] = cum_cost[q] + pd.n_items * pd.cost;
     }
-    const long long total_items = items;
+    const long long all_items = items;
+    const long long total_items = item_limit >= 0 ? std::min(item_limit, all_items) : all_items;
     const int cps = p->opt.ctas_per_sm ? p->opt.ctas_per_sm
-                    : (p->mode == BSH_MODE_BATCHED && p->smem <= smem_two ? 512 / p->threads : 1);
+                    : (p->mode == BSH_MODE_BATCHED && p->smem <= smem_two ? blocks_target : 1);
     const int k = p->top_k;
     // region item ranges
     std::vector<long long> r_begin(p->regions + 1, 0);
@@ -406,7 +437,7 @@ int build_schedule(bsh_plan* p) {
             r_prob[pd.region_base + pt] = q;
         }
     }
-    r_begin[p->regions] = total_items;
+    r_begin[p->regions] = all_items;
     p->region_problem.assign(r_prob.begin(), r_prob.end());
     std::vector<std::vector<int32_t>> rvis(p->regions);
     if (p->mode == BSH_MODE_BATCHED) {
@@ -416,10 +447,15 @@ int build_schedule(bsh_plan* p) {
         p->cta_item.assign(C + 1, 0);
         const long long T = cum_cost[p->n];
         for (long long c = 0; c <= C; ++c) {
-            const long long X = (long long)((__int128)T * c / C);
-            int q = 0;
-            while (q + 1 < p->n && X >= cum_cost[q + 1]) ++q;
-            long long it = p->P[q].pd.item_begin + (X - cum_cost[q]) / p->P[q].pd.cost;
+            long long it;
+            if (total_items < all_items) {
+                it = total_items * c / C;     // a slice for the autotuner: even split
+            } else {
+                const long long X = (long long)((__int128)T * c / C);
+                int q = 0;
+                while (q + 1 < p->n && X >= cum_cost[q + 1]) ++q;
+                it = p->P[q].pd.item_begin + (X - cum_cost[q]) / p->P[q].pd.cost;
+            }
             if (c == C) it = total_items;
             p->cta_item[c] = std::min(it, total_items);
         }
@@ -438,6 +474,7 @@ int build_schedule(bsh_plan* p) {
         }
         p->cta_visit[C] = v;
         p->visits = v;
+        p->visit_cap = (int)C + p->regions;   // bound for any split of the work list
     } else {
         // one launch per region, each with its own small persistent grid
         const long long Cmax = (long long)p->num_sms * cps;
@@ -461,6 +498,7 @@ int build_schedule(bsh_plan* p) {
         }
         p->pl_off[p->regions] = (int)p->cta_item.size();
         p->visits = v;
+        p->visit_cap = v;
         p->ctas = (int)Cmax;
     }
     p->region_visit_off.assign(p->regions + 1, 0);
@@ -490,11 +528,11 @@ int build_schedule(bsh_plan* p) {
     }
     p->off_cta_item = o; o = al(o + sizeof(int64_t) * p->cta_item.size());
     p->off_cta_visit = o; o = al(o + sizeof(int32_t) * p->cta_visit.size());
-    p->off_vbuf = o; o = al(o + sizeof(Entry) * (size_t)p->visits * p->cap);
-    p->off_vcount = o; o = al(o + sizeof(int32_t) * (size_t)std::max(1, p->visits));
+    p->off_vbuf = o; o = al(o + sizeof(Entry) * (size_t)p->visit_cap * p->cap);
+    p->off_vcount = o; o = al(o + sizeof(int32_t) * (size_t)std::max(1, p->visit_cap));
     p->off_rprob = o; o = al(o + sizeof(int32_t) * p->regions);
     p->off_rvoff = o; o = al(o + sizeof(int32_t) * (p->regions + 1));
-    p->off_rvis = o; o = al(o + sizeof(int32_t) * std::max<size_t>(1, p->region_visits.size()));
+    p->off_rvis = o; o = al(o + sizeof(int32_t) * (size_t)std::max(1, p->visit_cap));
     p->off_scratch = o; o = al(o + sizeof(Entry) * (size_t)p->regions * k);
     p->off_dense = o; o = al(o + 2 * sizeof(void*) * p->n);
     p->ws_size = o;
@@ -584,14 +622,10 @@ int run_count(bsh_plan* p, int dense, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" {
-
-int bsh_plan_bind(bsh_plan* p, void* workspace, size_t bytes, bsh_stream stream) {
-    if (!p) return BSH_ERR_ARG;
-    if (!workspace || bytes < p->ws_size) return BSH_ERR_WORKSPACE;
-    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BSH_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    p->ws = static_cast<unsigned char*>(workspace);
+namespace {
+// Points the descriptors at the workspace under the current layout, encodes the
+// peakgram tensor maps and uploads the small tables; synchronises `st`.
+int upload_plan(bsh_plan* p, cudaStream_t st) {
     std::vector<ProbDev> hp(p->n);
     for (int q = 0; q < p->n; ++q) {
         ProbHost& h = p->P[q];
@@ -644,17 +678,100 @@ int bsh_plan_bind(bsh_plan* p, void* workspace, size_t bytes, bsh_stream stream)
     e = e ? e : cudaMemsetAsync(p->ws + p->off_vcount, 0, sizeof(int32_t) * std::max(1, p->visits), st);
     e = e ? e : cudaStreamSynchronize(st);
     if (e) return BSH_ERR_CUDA;
+    return BSH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int bsh_plan_bind(bsh_plan* p, void* workspace, size_t bytes, bsh_stream stream) {
+    if (!p) return BSH_ERR_ARG;
+    if (!workspace || bytes < p->ws_cap) return BSH_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BSH_ERR_ARG;
+    p->ws = static_cast<unsigned char*>(workspace);
+    const int rc = upload_plan(p, (cudaStream_t)stream);
+    if (rc) return rc;
     p->bound = true;
     return BSH_OK;
 }
 
 int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     if (!p || !p->bound) return BSH_ERR_STATE;
-    (void)stream;
-    return BSH_OK;
+    if (p->mode != BSH_MODE_BATCHED) return BSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::vector<int> ths = tune_threads(p), chs = tune_chunks(p);
+    if (ths.size() * chs.size() <= 1) return BSH_OK;
+    double best_rate = -1.0;
+    int best_t = p->threads, best_c = p->chunk;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return BSH_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return BSH_ERR_CUDA;
+    }
+    int rc = BSH_OK;
+    for (int t : ths) {
+        for (int c : chs) {
+            p->threads = t;
+            p->chunk = c;
+            // a slice of the work list: about six items per CTA of this shape
+            const long long slice = (long long)p->num_sms * (512 / t) * 6;
+            if (build_schedule(p, slice) != BSH_OK || p->ws_size > p->ws_cap) continue;
+            if ((rc = upload_plan(p, st)) != BSH_OK) break;
+            // terms in the slice
+            double terms = 0.0;
+            for (long long it = 0; it < p->cta_item[p->ctas]; ++it) {
+                int q = 0;
+                while (q + 1 < p->n && it >= p->P[q + 1].pd.item_begin) ++q;
+                const ProbDev& pd = p->P[q].pd;
+                const long long loc = it - pd.item_begin;
+                const int rr = (int)(loc % ((long long)pd.n_fb * pd.n_bt));
+                const int fb = rr / pd.n_bt, bt = rr % pd.n_bt;
+                const int nb = std::min(t, pd.B - bt * t);
+                const int jb = std::min(pd.JB, pd.n_f0 - fb * pd.JB);
+                terms += (double)nb * jb * pd.N;
+            }
+            if ((rc = run_count(p, 0, st)) != BSH_OK) break;   // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 2 && rc == BSH_OK; ++r) rc = run_count(p, 0, st);
+            cudaEventRecord(e1, st);
+            if (rc != BSH_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = rc ? rc : BSH_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double rate = 2.0 * terms / (ms * 1e-3);
+            if (rate > best_rate) {
+                best_rate = rate;
+                best_t = t;
+                best_c = c;
+            }
+        }
+        if (rc != BSH_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->threads = best_t;
+    p->chunk = best_c;
+    const int rc2 = build_schedule(p);
+    if (rc2 != BSH_OK) return rc2;
+    const int rc3 = upload_plan(p, st);
+    if (rc != BSH_OK) return rc;
+    if (rc3 != BSH_OK) return rc3;
+    p->tuned_rate = best_rate;
+    return bsh_graph_reset(p);
 }
 
 int bsh_number_count(bsh_plan* p, bsh_stream stream) { return run_count(p, 0, (cudaStream_t)stream); }
+
+int bsh_plan_tile(const bsh_plan* p, int* threads, int* sft_chunk, int* ctas) {
+    if (!p || !threads || !sft_chunk || !ctas) return BSH_ERR_ARG;
+    *threads = p->threads;
+    *sft_chunk = p->chunk;
+    *ctas = p->ctas;
+    return BSH_OK;
+}
 
 int bsh_count_dense(bsh_plan* p, int32_t* const* n_unw, float* const* n_w, bsh_stream stream) {
     if (!p || !p->bound) return BSH_ERR_STATE;

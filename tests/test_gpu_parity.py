@@ -100,6 +100,36 @@ def test_count_dense_batched(mid_small, dtype):
     plan.close()
 
 
+@pytest.mark.parametrize("threads,chunk", [(128, 64), (256, 256), (128, 256)])
+def test_count_dense_tile_shapes(mid_small, threads, chunk):
+    pr = mid_small
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=chunk)
+    assert plan.tile()["threads"] == threads
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    check_dense(gu[0], gw[0], op.count_dense())
+    plan.close()
+
+
+def test_autotune_keeps_parity(mid_small):
+    pr = mid_small
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    tile = plan.autotune()
+    assert tile["threads"] in (128, 256) and tile["sft_chunk"] in (32, 64, 128, 256)
+    assert bsh.sync_status() == bsh.OK
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    check_dense(gu[0], gw[0], op.count_dense())
+    plan.number_count()
+    assert bsh.sync_status() == bsh.OK
+    _, sc = oracle_scores(op, wq)
+    by_patch = [sc[pr.patch_start[p]:pr.patch_start[p + 1]] for p in range(len(pr.patch_start) - 1)]
+    check_toplists(plan, dp, 0, by_patch, pr.top_k, tol=2e-4)
+    plan.close()
+
+
 def test_count_dense_plain_is_fp64_exact(mid_small):
     pr = mid_small
     dp, op, wq = device_problem(pr, "f64")
