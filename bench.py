@@ -56,14 +56,41 @@ def make_problem(kind: str, rank: int):
         sky = synth.fibonacci_sky(2000)
     else:
         sky = synth.fibonacci_sky(200)
-    if rank:
-        # each rank searches its own sky: the grid rotated about z by a rank-dependent angle
-        a = 2.399963 * rank
-        c, s = math.cos(a), math.sin(a)
-        sky = sky @ np.array([[c, s, 0.0], [-s, c, 0.0], [0.0, 0.0, 1.0]])
+    sky = rank_sky(sky, rank)
     if kind == "mid":
         return synth.mid(sky=sky)
     return synth.mid(n_sky=200, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky)
+
+
+def rank_sky(sky: np.ndarray, rank: int) -> np.ndarray:
+    """The sky grid searched by `rank`: rotated about z by a rank-dependent angle."""
+    if not rank:
+        return sky
+    a = 2.399963 * rank
+    c, s = math.cos(a), math.sin(a)
+    return sky @ np.array([[c, s, 0.0], [-s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value over ranks (control path only); x itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(terms_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput: every rank's terms over the slowest rank's time."""
+    return terms_per_rank * world / t_max
 
 
 def workload_config(pr, kind):
@@ -225,9 +252,7 @@ def main():
     from paper_1904_04873_gb300 import build as _build
     from paper_1904_04873_gb300 import bsh
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -289,14 +314,9 @@ def main():
     if st != bsh.OK:
         raise SystemExit(f"device status {st} in timed region")
 
-    t_max = elapsed
+    t_max = max_over_ranks(elapsed, "cuda")
     terms_rank = pr.n_terms * args.steps
-    terms_all = terms_rank * world
-    if world > 1:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = terms_all / t_max
+    value = weak_value(terms_rank, world, t_max)
 
     # ---- end to end through the public API: pinned host inputs -> device -> toplists -> host
     e2e = None
@@ -338,12 +358,8 @@ def main():
             d2h = e2e_step()
         a1.record(stream)
         torch.cuda.synchronize()
-        te = a0.elapsed_time(a1) / 1e3
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": pr.n_terms * ke * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        te = max_over_ranks(a0.elapsed_time(a1) / 1e3, "cuda")
+        e2e = {"value": weak_value(pr.n_terms * ke, world, te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     # ---- plain form (FP64 track per term, FP64 weights, one launch per patch) on a bounded sample

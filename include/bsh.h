@@ -190,6 +190,15 @@ int bsh_autotune(bsh_plan* plan, bsh_stream stream);
 /* Current tile shape: CTA size, SFTs per stage, persistent CTAs in the grid. */
 int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas);
 
+/* Weighted-accumulation variant of the batched count (also autotuned):
+ * 0 = one predicated FP32 add per term; 1 = per 8 SFTs a table of the 256
+ * subset sums of their weights and one lookup per template.  Both sum the
+ * same weights in FP32 within 4e-6 relative of their FP64 sum (Kahan
+ * compensation across 64-SFT blocks).  bsh_plan_set_accumulate drops a
+ * recorded graph. */
+int bsh_plan_set_accumulate(bsh_plan* plan, int variant);
+int bsh_plan_accumulate(const bsh_plan* plan);
+
 /* ------------------------------------------------------------------------ */
 /* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */
 /* sum n = sum_i w_i * bit_i[k_i] along the track k_i = round(f(t_i) T_c) of  */

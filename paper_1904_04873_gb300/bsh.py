@@ -80,6 +80,8 @@ _SIGS = {
     "bsh_plan_first_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bsh_plan_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "bsh_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_plan_set_accumulate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bsh_plan_accumulate": (ctypes.c_int, [ctypes.c_void_p]),
     "bsh_plan_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int)]),
     "bsh_number_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -295,7 +297,11 @@ class Plan:
     def tile(self):
         t, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().bsh_plan_tile(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g)), "bsh_plan_tile")
-        return {"threads": t.value, "sft_chunk": c.value, "ctas": g.value}
+        return {"threads": t.value, "sft_chunk": c.value, "ctas": g.value,
+                "accumulate": lib().bsh_plan_accumulate(self.h)}
+
+    def set_accumulate(self, variant: int):
+        _check(lib().bsh_plan_set_accumulate(self.h, variant), "bsh_plan_set_accumulate")
 
     def close(self):
         if self.h:

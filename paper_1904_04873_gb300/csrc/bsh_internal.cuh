@@ -269,6 +269,7 @@ struct CountArgs {
     int mode;                    // BSH_MODE_*
     int max_n;                   // largest SFT count of the problems
     int wrows;                   // Omega-T rows one warp needs at most
+    int acc_mode;                // weighted accumulation variant of the batched kernel
 };
 
 struct TmapSet {

@@ -99,7 +99,7 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 // per-thread Kahan sums, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, cp, acc, comp, bar, done, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, cp, acc, comp, tab, bar, done, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
@@ -116,6 +116,7 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     L.cp = o; o = align128(o + nw * I * wrows * 8);
     L.acc = o; o = align128(o + JW * threads * 4);
     L.comp = o; o = align128(o + JW * threads * 4);
+    L.tab = o; o = align128(o + nw * 256 * 4);
     L.bar = o; o = align128(o + 16);
     L.done = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
@@ -179,6 +180,19 @@ __device__ __forceinline__ void issue_stage(const CountArgs& a, const TmapSet& m
     bulk_load(smem + L.w[buf], P.w32 + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
     for (int r = 0; r < c.nrows; ++r)
         bulk_load(smem + L.c[buf] + r * I * 4, P.c_q + (size_t)(c.ot0 + r) * P.Np + i0, (uint32_t)(I * 4), bar);
+}
+
+// 8 x 8 bit-matrix transpose: byte u of x is row u (bit k = column k); on
+// return byte k holds column k (bit u = bit k of the input's byte u).
+__device__ __forceinline__ uint64_t transpose8x8(uint64_t x) {
+    uint64_t t;
+    t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x = x ^ t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x = x ^ t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x = x ^ t ^ (t << 28);
+    return x;
 }
 
 __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
@@ -330,7 +344,11 @@ __device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, 
     return true;
 }
 
-template <int THREADS, int NE>
+// ACC selects the weighted accumulation: 0 = one predicated FP32 add per term;
+// 1 = per 8 SFTs, a warp-private table of the 256 subset sums of their weights
+// and one lookup per f0 template (the 8 window masks are bit-transposed so
+// that byte j holds template j's 8 bits).
+template <int THREADS, int NE, int ACC>
 __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -347,6 +365,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     const int wrows = a.wrows;
     int2* yp = reinterpret_cast<int2*>(smem + L.y) + warp * I;
     int2* cp = reinterpret_cast<int2*>(smem + L.cp) + warp * I * wrows;
+    float* tab = reinterpret_cast<float*>(smem + L.tab) + warp * 256;
 
     long long it = a.cta_item[blockIdx.x];
     const long long it_end = a.cta_item[blockIdx.x + 1];
@@ -478,13 +497,47 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const uint32_t m = mk[u] & jmask;
-                    mk[u] = m;
-                    const float wv = wt[g8 + u];
+                for (int u = 0; u < 8; ++u) mk[u] &= jmask;
+                if (ACC == 0) {
 #pragma unroll
-                    for (int j = 0; j < JW; ++j)
-                        if (m & (1u << j)) part[j] += wv;
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t m = mk[u];
+                        const float wv = wt[g8 + u];
+#pragma unroll
+                        for (int j = 0; j < JW; ++j)
+                            if (m & (1u << j)) part[j] += wv;
+                    }
+                } else {
+                    // subset sums of the 8 weights: entry 32 m + l = low(l) + high(m)
+                    const float* wg = wt + g8;
+                    float lo = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 5; ++u)
+                        if ((lane >> u) & 1) lo += wg[u];
+                    const float w5 = wg[5], w6 = wg[6], w7 = wg[7];
+                    const float h3 = w5 + w6;
+                    __syncwarp();                 // the previous group's lookups are done
+                    tab[lane] = lo;
+                    tab[32 + lane] = lo + w5;
+                    tab[64 + lane] = lo + w6;
+                    tab[96 + lane] = lo + h3;
+                    tab[128 + lane] = lo + w7;
+                    tab[160 + lane] = lo + (w5 + w7);
+                    tab[192 + lane] = lo + (w6 + w7);
+                    tab[224 + lane] = lo + (h3 + w7);
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const unsigned sel = (unsigned)q | ((unsigned)(q + 4) << 4);
+                        const uint32_t a01 = __byte_perm(mk[0], mk[1], sel);
+                        const uint32_t a23 = __byte_perm(mk[2], mk[3], sel);
+                        const uint32_t a45 = __byte_perm(mk[4], mk[5], sel);
+                        const uint32_t a67 = __byte_perm(mk[6], mk[7], sel);
+                        const uint64_t x = transpose8x8(((uint64_t)__byte_perm(a45, a67, 0x5410) << 32) |
+                                                        (uint64_t)__byte_perm(a01, a23, 0x5410));
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) part[8 * q + k] += tab[(unsigned)(x >> (8 * k)) & 0xffu];
+                    }
                 }
                 uint32_t tA, tB, fA, fB, eights;
                 csa(tA, ones, ones, mk[0], mk[1]);
@@ -638,27 +691,26 @@ void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads
         return;
     }
     const bool small_n = a.max_n < 8 * 1024;
+#define BSH_LAUNCH_BATCHED(T, NE, ACC)                                            \
+    do {                                                                          \
+        static int s_done = 0;                                                    \
+        ensure_smem(count_batched<T, NE, ACC>, a.smem_bytes, &s_done);            \
+        count_batched<T, NE, ACC><<<grid, T, a.smem_bytes, st>>>(a, maps);        \
+    } while (0)
     if (threads == 128) {
         if (small_n) {
-            static int s_b128_10 = 0;
-            ensure_smem(count_batched<128, 10>, a.smem_bytes, &s_b128_10);
-            count_batched<128, 10><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+            if (a.acc_mode) BSH_LAUNCH_BATCHED(128, 10, 1); else BSH_LAUNCH_BATCHED(128, 10, 0);
         } else {
-            static int s_b128_13 = 0;
-            ensure_smem(count_batched<128, 13>, a.smem_bytes, &s_b128_13);
-            count_batched<128, 13><<<grid, 128, a.smem_bytes, st>>>(a, maps);
+            if (a.acc_mode) BSH_LAUNCH_BATCHED(128, 13, 1); else BSH_LAUNCH_BATCHED(128, 13, 0);
         }
     } else {
         if (small_n) {
-            static int s_b256_10 = 0;
-            ensure_smem(count_batched<256, 10>, a.smem_bytes, &s_b256_10);
-            count_batched<256, 10><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+            if (a.acc_mode) BSH_LAUNCH_BATCHED(256, 10, 1); else BSH_LAUNCH_BATCHED(256, 10, 0);
         } else {
-            static int s_b256_13 = 0;
-            ensure_smem(count_batched<256, 13>, a.smem_bytes, &s_b256_13);
-            count_batched<256, 13><<<grid, 256, a.smem_bytes, st>>>(a, maps);
+            if (a.acc_mode) BSH_LAUNCH_BATCHED(256, 13, 1); else BSH_LAUNCH_BATCHED(256, 13, 0);
         }
     }
+#undef BSH_LAUNCH_BATCHED
 }
 
 }  // namespace bsh

@@ -103,6 +103,7 @@ struct bsh_plan {
     int regions = 0, visits = 0, visit_cap = 0;
     size_t ws_cap = 0;                     // workspace bytes: the largest of the tuning candidates
     double tuned_rate = 0.0;
+    int acc_mode = 0;                      // weighted accumulation variant (autotuned)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
@@ -594,6 +595,7 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.ot_max = p->ot_max;
     a.mode = p->mode;
     a.wrows = p->wrows;
+    a.acc_mode = p->acc_mode;
     a.max_n = 0;
     for (auto& h : p->P) a.max_n = std::max(a.max_n, h.d.N);
     return a;
@@ -702,7 +704,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     const std::vector<int> ths = tune_threads(p), chs = tune_chunks(p);
     if (ths.size() * chs.size() <= 1) return BSH_OK;
     double best_rate = -1.0;
-    int best_t = p->threads, best_c = p->chunk;
+    int best_t = p->threads, best_c = p->chunk, best_a = p->acc_mode;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return BSH_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -710,13 +712,20 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
         return BSH_ERR_CUDA;
     }
     int rc = BSH_OK;
+    std::vector<long long> tried;
     for (int t : ths) {
         for (int c : chs) {
+          for (int am = 0; am < 2; ++am) {
             p->threads = t;
             p->chunk = c;
+            p->acc_mode = am;
             // a slice of the work list: about six items per CTA of this shape
             const long long slice = (long long)p->num_sms * (512 / t) * 6;
             if (build_schedule(p, slice) != BSH_OK || p->ws_size > p->ws_cap) continue;
+            // the stage may have been shrunk to fit shared memory: time each effective shape once
+            const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | am;
+            if (std::find(tried.begin(), tried.end(), key) != tried.end()) continue;
+            tried.push_back(key);
             if ((rc = upload_plan(p, st)) != BSH_OK) break;
             // terms in the slice
             double terms = 0.0;
@@ -746,7 +755,10 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 best_rate = rate;
                 best_t = t;
                 best_c = c;
+                best_a = am;
             }
+          }
+          if (rc != BSH_OK) break;
         }
         if (rc != BSH_OK) break;
     }
@@ -754,6 +766,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     cudaEventDestroy(e1);
     p->threads = best_t;
     p->chunk = best_c;
+    p->acc_mode = best_a;
     const int rc2 = build_schedule(p);
     if (rc2 != BSH_OK) return rc2;
     const int rc3 = upload_plan(p, st);
@@ -772,6 +785,14 @@ int bsh_plan_tile(const bsh_plan* p, int* threads, int* sft_chunk, int* ctas) {
     *ctas = p->ctas;
     return BSH_OK;
 }
+
+int bsh_plan_set_accumulate(bsh_plan* p, int variant) {
+    if (!p || (variant != 0 && variant != 1)) return BSH_ERR_ARG;
+    p->acc_mode = variant;
+    return bsh_graph_reset(p);
+}
+
+int bsh_plan_accumulate(const bsh_plan* p) { return p ? p->acc_mode : -1; }
 
 int bsh_count_dense(bsh_plan* p, int32_t* const* n_unw, float* const* n_w, bsh_stream stream) {
     if (!p || !p->bound) return BSH_ERR_STATE;

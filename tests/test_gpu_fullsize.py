@@ -1,0 +1,90 @@
+"""Full-size sampled parity on the benchmark workload (mid: 2 x 2000 SFTs,
+2000 sky points in 40 patches, 32^3 binary templates, 90 f0 bins, top-1000),
+in the launch configuration bench.py times (autotuned batched plan).
+
+The oracle cannot count 5.9e9 templates, so it recomputes sampled outputs
+one template at a time: toplist entries (counts, s_H, P), and random
+templates outside the lists, whose oracle s_H must not exceed the list's
+k-th score (the toplist property).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_04873_gb300 import bsh, synth
+from gpu_common import REL_TOL, device_problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1904_04873_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    pr = synth.mid()
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    plan.autotune()
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(100)
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    plan.close()
+    return pr, op, wq, lists
+
+
+def _score(op, wq, s, b, j):
+    c = op.count_one(s, b, j)
+    sH = oracle.significance(c["n_w"], wq[s].sum(), (wq[s] ** 2).sum())
+    return c, float(sH)
+
+
+def test_sampled_toplist_entries(run):
+    pr, op, wq, lists = run
+    rng = np.random.default_rng(8)
+    per_s = pr.B * pr.n_f0
+    patches = [0, len(lists) - 1] + list(rng.choice(len(lists), 2, replace=False))
+    for p in patches:
+        g = lists[p]
+        assert g.size == pr.top_k
+        assert np.all(np.diff(g["s_h"]) <= 0)
+        pick = list(range(10)) + list(rng.choice(np.arange(10, g.size), 20, replace=False))
+        for e in pick:
+            c = g[e]
+            s, rem = divmod(int(c["template_id"]), per_s)
+            b, j = divmod(rem, pr.n_f0)
+            assert pr.patch_start[p] <= s < pr.patch_start[p + 1]
+            ref, sH = _score(op, wq, s, b, j)
+            assert ref["unw_lo"] <= int(c["n_unw"]) <= ref["unw_hi"]
+            assert abs(float(c["n_w"]) - ref["n_w"]) <= REL_TOL * ref["n_w"]
+            assert abs(float(c["s_h"]) - sH) < 2e-4
+            if e < 10:
+                P = op.power_sum(s, b, j) if op.rho is not None else None
+                if P is not None:
+                    assert abs(float(c["power"]) - P) <= REL_TOL * P
+
+
+def test_random_templates_respect_the_kth_score(run):
+    pr, op, wq, lists = run
+    rng = np.random.default_rng(9)
+    per_s = pr.B * pr.n_f0
+    for p in rng.choice(len(lists), 3, replace=False):
+        g = lists[p]
+        kth = float(g["s_h"][-1])
+        ids = set(int(x) for x in g["template_id"])
+        s0, s1 = pr.patch_start[p], pr.patch_start[p + 1]
+        for _ in range(150):
+            s = int(rng.integers(s0, s1))
+            b = int(rng.integers(pr.B))
+            j = int(rng.integers(pr.n_f0))
+            tid = (s * pr.B + b) * pr.n_f0 + j
+            if tid in ids:
+                continue
+            _, sH = _score(op, wq, s, b, j)
+            assert sH <= kth + 2e-4, (p, s, b, j, sH, kth)

@@ -100,12 +100,14 @@ def test_count_dense_batched(mid_small, dtype):
     plan.close()
 
 
-@pytest.mark.parametrize("threads,chunk", [(128, 64), (256, 256), (128, 256)])
-def test_count_dense_tile_shapes(mid_small, threads, chunk):
+@pytest.mark.parametrize("threads,chunk,acc", [(128, 64, 0), (256, 256, 0), (128, 256, 1), (256, 64, 1),
+                                               (256, 128, 1)])
+def test_count_dense_tile_shapes(mid_small, threads, chunk, acc):
     pr = mid_small
     dp, op, wq = device_problem(pr, "f16")
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=chunk)
-    assert plan.tile()["threads"] == threads
+    plan.set_accumulate(acc)
+    assert plan.tile()["threads"] == threads and plan.tile()["accumulate"] == acc
     gu, gw = plan.count_dense()
     assert bsh.sync_status() == bsh.OK
     check_dense(gu[0], gw[0], op.count_dense())
@@ -118,6 +120,7 @@ def test_autotune_keeps_parity(mid_small):
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
     tile = plan.autotune()
     assert tile["threads"] in (128, 256) and tile["sft_chunk"] in (32, 64, 128, 256)
+    assert tile["accumulate"] in (0, 1)
     assert bsh.sync_status() == bsh.OK
     gu, gw = plan.count_dense()
     assert bsh.sync_status() == bsh.OK
