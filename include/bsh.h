@@ -194,8 +194,10 @@ int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas)
  * 0 = one predicated FP32 add per term; 1 = per 8 SFTs a table of the 256
  * subset sums of their weights and one lookup per template.  Both sum the
  * same weights in FP32 within 4e-6 relative of their FP64 sum (Kahan
- * compensation across 64-SFT blocks).  bsh_plan_set_accumulate drops a
- * recorded graph. */
+ * compensation across 64-SFT blocks).  bsh_plan_set_accumulate re-derives
+ * the SFT stage for the variant's shared-memory layout, re-uploads a bound
+ * plan (synchronising the legacy default stream) and drops a recorded graph;
+ * not capturable. */
 int bsh_plan_set_accumulate(bsh_plan* plan, int variant);
 int bsh_plan_accumulate(const bsh_plan* plan);
 
@@ -252,6 +254,22 @@ int bsh_power_sum(bsh_plan* plan, bsh_cand* cands, const int32_t* n_cands, int n
 int bsh_graph_launch(bsh_plan* plan, bsh_cand* cands, int32_t* n_cands, int n_cf,
                      bsh_cand* final_list, int32_t* n_final, bsh_stream stream);
 int bsh_graph_reset(bsh_plan* plan);
+
+/* ------------------------------------------------------------------------ */
+/* Track diagnostics, Eq. (15).                                              */
+/* bsh_track_precision: for every term of sky points [s_begin, s_end) of the */
+/* plan's problem (every binary template, SFT and f0 template) compares the  */
+/* exact FP64 bin with (a) the same expression evaluated in single          */
+/* precision and (b) the fixed-point bin of the batched kernels.  counts [4] */
+/* DEVICE uint64: terms, single-precision mismatches, fixed-point mismatches */
+/* outside the tie band, terms inside the 1e-9-bin tie band.  Capturable.    */
+/* bsh_track_bins: exact bins of listed templates (ids as in bsh_cand) in   */
+/* every SFT: bins [n][N] DEVICE int32 (bin numbers, not band columns), e.g. */
+/* to place injected signals.  Capturable.                                   */
+/* ------------------------------------------------------------------------ */
+int bsh_track_precision(bsh_plan* plan, int problem, int s_begin, int s_end, unsigned long long* counts,
+                        bsh_stream stream);
+int bsh_track_bins(bsh_plan* plan, int problem, const int64_t* ids, int n, int32_t* bins, bsh_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Host-side checks of the fixed-point track (no GPU needed).                 */

@@ -92,6 +92,10 @@ _SIGS = {
     "bsh_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_graph_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_track_precision": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_track_bins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_power_sum_static": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
@@ -302,6 +306,25 @@ class Plan:
 
     def set_accumulate(self, variant: int):
         _check(lib().bsh_plan_set_accumulate(self.h, variant), "bsh_plan_set_accumulate")
+
+    def track_precision(self, problem: int = 0, s_begin: int = 0, s_end: Optional[int] = None, stream=None):
+        """Counts of (terms, single-precision bin mismatches, fixed-point mismatches, tie-band terms)."""
+        import torch
+        if s_end is None:
+            s_end = self.problems[problem].pr.S
+        c = torch.zeros(4, dtype=torch.int64, device=self.problems[problem].device)
+        _check(lib().bsh_track_precision(self.h, problem, s_begin, s_end, _ptr(c), _stream(stream)),
+               "bsh_track_precision")
+        return [int(x) for x in c.cpu().tolist()]
+
+    def track_bins(self, template_ids, problem: int = 0, stream=None):
+        """Exact bins [n][N] of the listed templates (device int32)."""
+        import torch
+        ids = template_ids.contiguous()
+        out = torch.empty((ids.numel(), self.problems[problem].pr.N), dtype=torch.int32, device=ids.device)
+        _check(lib().bsh_track_bins(self.h, problem, _ptr(ids), ids.numel(), _ptr(out), _stream(stream)),
+               "bsh_track_bins")
+        return out
 
     def close(self):
         if self.h:

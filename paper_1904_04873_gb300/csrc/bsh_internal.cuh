@@ -311,5 +311,7 @@ struct PowerArgs {
     unsigned* status;
 };
 void launch_power(const PowerArgs& a, int regions, cudaStream_t st);
+void launch_precision(const ProbDev* dprob, int s_begin, int s_end, unsigned long long* counts, cudaStream_t st);
+void launch_bins(const ProbDev* dprob, const int64_t* ids, int n, int32_t* bins, unsigned* status, cudaStream_t st);
 
 }  // namespace bsh

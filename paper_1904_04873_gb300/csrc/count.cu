@@ -104,7 +104,7 @@ struct Layout {
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
 
-__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads) {
+__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc) {
     Layout L;
     const int nw = threads / 32;
     int o = 0;
@@ -116,7 +116,7 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     L.cp = o; o = align128(o + nw * I * wrows * 8);
     L.acc = o; o = align128(o + JW * threads * 4);
     L.comp = o; o = align128(o + JW * threads * 4);
-    L.tab = o; o = align128(o + nw * 256 * 4);
+    L.tab = o; o = align128(o + (acc ? nw * 256 * 4 : 0));
     L.bar = o; o = align128(o + 16);
     L.done = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NW = THREADS / 32;
-    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max, a.wrows, THREADS);
+    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max, a.wrows, THREADS, ACC);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
     unsigned* done = reinterpret_cast<unsigned*>(smem + L.done);
     SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem + L.sel);
@@ -671,9 +671,9 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
 
 }  // namespace
 
-int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads) {
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc) {
     if (mode == BSH_MODE_PLAIN) return align128((int)sizeof(SelectSmem)) + align128((int)sizeof(TopSmem));
-    return make_layout(I, wseg, ot_max, wrows, threads).total;
+    return make_layout(I, wseg, ot_max, wrows, threads, acc).total;
 }
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st) {

@@ -13,7 +13,7 @@
 #include "bsh_internal.cuh"
 
 namespace bsh {
-int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads);
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc);
 }
 
 using namespace bsh;
@@ -335,15 +335,18 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     size_t cap = 0;
     int first_rc = -1;
     for (int t : tune_threads(p))
-        for (int c : tune_chunks(p)) {
-            p->threads = t;
-            p->chunk = c;
-            const int rc = build_schedule(p);
-            if (first_rc < 0) first_rc = rc;
-            if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
-        }
+        for (int c : tune_chunks(p))
+            for (int am = 0; am < 2; ++am) {
+                p->threads = t;
+                p->chunk = c;
+                p->acc_mode = am;
+                const int rc = build_schedule(p);
+                if (first_rc < 0) first_rc = rc;
+                if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
+            }
     p->threads = tune_threads(p)[0];
     p->chunk = tune_chunks(p)[0];
+    p->acc_mode = 0;
     const int rc = build_schedule(p);
     if (rc) {
         delete p;
@@ -399,14 +402,14 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     const int smem_two = (227 * 1024) / blocks_target - 1024, smem_one = 220 * 1024;
     const int chunk0 = p->chunk;
     while (true) {
-        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads);
+        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode);
         if (p->smem <= smem_two || p->chunk <= 32) break;
         p->chunk /= 2;
     }
     if (p->smem > smem_two) {
         p->chunk = chunk0;
         while (true) {
-            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads);
+            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode);
             if (p->smem <= smem_one || p->chunk <= 32) break;
             p->chunk /= 2;
         }
@@ -789,10 +792,45 @@ int bsh_plan_tile(const bsh_plan* p, int* threads, int* sft_chunk, int* ctas) {
 int bsh_plan_set_accumulate(bsh_plan* p, int variant) {
     if (!p || (variant != 0 && variant != 1)) return BSH_ERR_ARG;
     p->acc_mode = variant;
+    p->chunk = tune_chunks(p)[0];
+    const int rc = build_schedule(p);
+    if (rc) return rc;
+    if (p->bound) {
+        const int rc2 = upload_plan(p, nullptr);
+        if (rc2) return rc2;
+    }
     return bsh_graph_reset(p);
 }
 
 int bsh_plan_accumulate(const bsh_plan* p) { return p ? p->acc_mode : -1; }
+
+int bsh_track_precision(bsh_plan* p, int problem, int s_begin, int s_end, unsigned long long* counts,
+                        bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (problem < 0 || problem >= p->n || !counts) return BSH_ERR_ARG;
+    const ProbDev& hp = p->P[problem].pd;
+    if (s_begin < 0 || s_end > hp.S || s_begin > s_end) return BSH_ERR_ARG;
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ProbDev* dprob = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs) + problem;
+    if (cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) return BSH_ERR_CUDA;
+    launch_tables(hp, dprob, p->mode, sp, st);
+    launch_precision(dprob, s_begin, s_end, counts, st);
+    return cuda_fail(cudaGetLastError());
+}
+
+int bsh_track_bins(bsh_plan* p, int problem, const int64_t* ids, int n, int32_t* bins, bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (problem < 0 || problem >= p->n || n < 0 || (n > 0 && (!ids || !bins))) return BSH_ERR_ARG;
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ProbDev* dprob = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs) + problem;
+    launch_tables(p->P[problem].pd, dprob, p->mode, sp, st);
+    launch_bins(dprob, ids, n, bins, sp, st);
+    return cuda_fail(cudaGetLastError());
+}
 
 int bsh_count_dense(bsh_plan* p, int32_t* const* n_unw, float* const* n_w, bsh_stream stream) {
     if (!p || !p->bound) return BSH_ERR_STATE;
