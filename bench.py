@@ -401,9 +401,10 @@ def main():
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
     # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the
-    # 3.7 thread instructions per term measured by ncu (profiles/count_batched_small_full.md)
-    roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / 3.7, "instr_per_term": 3.7,
-                       "frac": count_rate / (n_sm * 128.0 * f_max / 3.7)}
+    # 3.55 thread instructions per term measured by ncu (profiles/count_batched_small_full.md)
+    ipt = 3.55
+    roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / ipt, "instr_per_term": ipt,
+                       "frac": count_rate / (n_sm * 128.0 * f_max / ipt)}
 
     cpu = None
     if not args.no_cpu and rank == 0:

@@ -407,7 +407,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         const int ot = bvalid ? b / P.n_ap - otw0 : 0;
         const int orow0 = otw0 - cur.ot0;                       // their offset in the CTA's staged rows
         const int apq = bvalid ? P.ap_q[iap] : 0;
-        const uint32_t jmask = bvalid ? (cur.jb >= 32 ? 0xffffffffu : ((1u << cur.jb) - 1u)) : 0u;
         const int s_y = P.fp.s_y, M = P.fp.M;
         const int wseg = a.wseg_max;
         const int pos_max = 32 * wseg - 33;
@@ -439,6 +438,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         for (int k = 0; k < NE; ++k) e8[k] = 0;
 
         const int F2a = cur.F2a, F2b = cur.F2a + 62;
+        const FixedPoint fpl = P.fp;
         bool aborted = false;
         for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
             const int buf = g & 1;
@@ -455,12 +455,12 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
             const int32_t* cr = reinterpret_cast<const int32_t*>(smem + L.c[buf]);
             for (int e = lane; e < I; e += 32) {
                 const int vq = vnr[e];
-                yp[e] = make_int2(make_Z(F2a, vq, P.fp), make_Z(F2b, vq, P.fp));
+                yp[e] = make_int2(make_Z(F2a, vq, fpl), make_Z(F2b, vq, fpl));
             }
             for (int e = lane; e < I * nrw; e += 32) {
                 const int r = e / I, il = e - r * I;
                 const int cq = cr[(orow0 + r) * I + il];
-                cp[il * wrows + r] = make_int2(make_C(F2a, cq, P.fp), make_C(F2b, cq, P.fp));
+                cp[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
             }
             __syncwarp();
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
@@ -476,10 +476,11 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     const int2 cc = cp[il * wrows + ot];
                     const int v0 = z.x - __mulhi(apq, cc.x);
                     const int v1 = z.y - __mulhi(apq, cc.y);
-                    const int pos = pbase + (v0 >> s_y);
-                    const bool fast = fp_fast(v0, v1, s_y, M) && (unsigned)pos <= (unsigned)pos_max;
-                    mk[u] = row_window(pk + il * wseg, fast ? pos : 0);
-                    slow |= (fast ? 0u : 1u) << u;
+                    // in the staged segment by construction (host band check, device velocity
+                    // check); the clamp only keeps the read in bounds
+                    const unsigned pos = min((unsigned)(pbase + (v0 >> s_y)), (unsigned)pos_max);
+                    mk[u] = row_window(pk + il * wseg, (int)pos);
+                    slow |= (fp_fast(v0, v1, s_y, M) ? 0u : 1u) << u;
                 }
                 if (slow) {       // rare: boundary crossing or near-boundary terms
 #pragma unroll 1
@@ -496,8 +497,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                                     : 0u;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) mk[u] &= jmask;
                 if (ACC == 0) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -539,6 +538,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                         for (int k = 0; k < 8; ++k) part[8 * q + k] += tab[(unsigned)(x >> (8 * k)) & 0xffu];
                     }
                 }
+                // (bits of templates past the block or of an invalid binary index are
+                // accumulated but never emitted)
                 uint32_t tA, tB, fA, fB, eights;
                 csa(tA, ones, ones, mk[0], mk[1]);
                 csa(tB, ones, ones, mk[2], mk[3]);

@@ -722,8 +722,8 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
             p->threads = t;
             p->chunk = c;
             p->acc_mode = am;
-            // a slice of the work list: about six items per CTA of this shape
-            const long long slice = (long long)p->num_sms * (512 / t) * 6;
+            // a slice of the work list: about sixteen items per CTA of this shape
+            const long long slice = (long long)p->num_sms * (512 / t) * 16;
             if (build_schedule(p, slice) != BSH_OK || p->ws_size > p->ws_cap) continue;
             // the stage may have been shrunk to fit shared memory: time each effective shape once
             const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | am;
@@ -744,16 +744,21 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 terms += (double)nb * jb * pd.N;
             }
             if ((rc = run_count(p, 0, st)) != BSH_OK) break;   // warm-up
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 2 && rc == BSH_OK; ++r) rc = run_count(p, 0, st);
-            cudaEventRecord(e1, st);
-            if (rc != BSH_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = rc ? rc : BSH_ERR_CUDA;
-                break;
+            float ms = 3.0e38f;
+            for (int r = 0; r < 3 && rc == BSH_OK; ++r) {      // best of three
+                cudaEventRecord(e0, st);
+                rc = run_count(p, 0, st);
+                cudaEventRecord(e1, st);
+                if (rc != BSH_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = rc ? rc : BSH_ERR_CUDA;
+                    break;
+                }
+                float m = 0.f;
+                cudaEventElapsedTime(&m, e0, e1);
+                ms = std::min(ms, m);
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double rate = 2.0 * terms / (ms * 1e-3);
+            if (rc != BSH_OK) break;
+            const double rate = terms / (ms * 1e-3);
             if (rate > best_rate) {
                 best_rate = rate;
                 best_t = t;
