@@ -183,62 +183,80 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline_sample(pr, budget_s: float = 12.0):
-    """Time the FP64 oracle on whole templates of sky point 0 (all SFTs, all f0
-    bins, the first nb binary templates); returns (terms/s, sample text)."""
+def _oracle_worker(args):
+    """Spawned process: time the oracle on binary templates [b0, b1) of sky point 0."""
+    (bits, w, v, t, F0, n_f0, sky, a_p, Om, Ta, k_lo, K, b0, b1) = args
+    import sys
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
     import oracle
+    op = oracle.OracleProblem(bits=bits, w=w, v=v, t=t, F0=F0, n_f0=n_f0, sky=sky, a_p=a_p, Omega=Om,
+                              T_asc=Ta, k_lo=k_lo, K=K)
+    t0 = time.perf_counter()
+    for b in range(b0, b1):
+        for j in range(n_f0):
+            op.count_one(0, b, j)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_sample(pr, budget_s: float = 12.0, procs: int = 0):
+    """Time the FP64 oracle on whole templates of sky point 0 (all SFTs, all f0
+    bins, a block of binary templates per process), with one process per host
+    core; returns (terms/s, cores, sample text)."""
+    import multiprocessing as mp
+    import oracle
+    procs = procs or (os.cpu_count() or 1)
     rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
     w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    op = oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky[:1],
-                              a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K)
-    t0 = time.perf_counter()
-    for b in range(2):
-        for j in range(pr.n_f0):
-            op.count_one(0, b, j)
-    dt = time.perf_counter() - t0
-    per_b = dt / 2
-    nb = max(2, min(pr.B, int(budget_s / max(per_b, 1e-6))))
-    t0 = time.perf_counter()
-    for b in range(nb):
-        for j in range(pr.n_f0):
-            op.count_one(0, b, j)
-    dt = time.perf_counter() - t0
-    terms = nb * pr.n_f0 * pr.N
-    return terms / dt, f"oracle count of sky point 0 x {nb} binary templates x {pr.n_f0} f0 x {pr.N} SFTs " \
-                       f"({terms:.3g} terms, {dt:.1f} s, single thread)"
+    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.k_lo, pr.K)
+    per_b = _oracle_worker(base + (0, 2)) / 2          # calibration, in this process
+    nb = max(1, min(pr.B // procs, int(budget_s / max(per_b, 1e-6))))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        times = pool.map(_oracle_worker, [base + (q * nb, (q + 1) * nb) for q in range(procs)])
+    dt = max(times)
+    terms = procs * nb * pr.n_f0 * pr.N
+    return terms / dt, procs, (f"oracle count of sky point 0 x {procs * nb} binary templates x {pr.n_f0} f0 x "
+                               f"{pr.N} SFTs ({terms:.3g} terms), {procs} spawned processes of {nb} binaries "
+                               f"each, slowest {dt:.1f} s")
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on every host core
+    (spawned processes sharded by binary template), a bounded sample per step."""
+    import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     pr = make_problem(args.workload, 0)
     import oracle
+    procs = os.cpu_count() or 1
     rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
     w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    op = oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky[:1],
-                              a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K)
-    nb = 16
+    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.k_lo, pr.K)
+    per_b = _oracle_worker(base + (0, 1))
+    nb = max(1, min(pr.B // (procs * max(1, args.steps + args.warmup)), int(1.5 / max(per_b, 1e-6))))
 
-    def step(b0):
-        for b in range(b0, b0 + nb):
-            for j in range(pr.n_f0):
-                op.count_one(0, b % pr.B, j)
+    def shards(step):
+        b0 = step * procs * nb
+        return [base + (b0 + q * nb, b0 + (q + 1) * nb) for q in range(procs)]
 
-    for k in range(args.warmup):
-        step(k * nb)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        step((args.warmup + k) * nb)
-    dt = time.perf_counter() - t0
-    terms = args.steps * nb * pr.n_f0 * pr.N
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for k in range(args.warmup):
+            pool.map(_oracle_worker, shards(k))
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            pool.map(_oracle_worker, shards(args.warmup + k))
+        dt = time.perf_counter() - t0
+    terms = args.steps * procs * nb * pr.n_f0 * pr.N
     v = terms / dt
-    sample = f"per step: oracle count of sky point 0 x {nb} binary templates x {pr.n_f0} f0 x {pr.N} SFTs"
+    sample = (f"per step: oracle count of sky point 0 x {procs * nb} binary templates x {pr.n_f0} f0 x {pr.N} SFTs "
+              f"on {procs} spawned processes")
     print(json.dumps({"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "impl": "reference", "config": workload_config(pr, args.workload),
-                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -408,8 +426,8 @@ def main():
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        v, sample = cpu_baseline_sample(pr)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        v, cores, sample = cpu_baseline_sample(pr)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
