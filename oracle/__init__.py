@@ -12,6 +12,9 @@ Parity status per function (each pinned by ``tests/test_oracle_*.py``):
   quantize        pinned (numpy float16, exact rational rounding)
   track           pinned (50-digit mpmath evaluation; a_p = 0 / v = 0 special cases;
                   period shift of t_asc; exact forced ties)
+  ELL1 track      pinned (exact Keplerian orbit of Eq. (6)-(10) solved independently:
+                  agreement to O(e^2); circular limit bitwise; t_asc period shift;
+                  grid layout against single-orbit problems)
   count           pinned (all-ones / all-zeros peakgrams, single-bit hits, linearity,
                   SFT-permutation invariance, noise mean and variance, injection)
   significance    pinned (Monte-Carlo mean / variance of Bernoulli peakgrams)
@@ -56,6 +59,7 @@ class Problem(ctypes.Structure):
         ("n_ap", ctypes.c_int), ("ap", ctypes.c_void_p), ("n_Om", ctypes.c_int),
         ("Om", ctypes.c_void_p), ("n_T", ctypes.c_int), ("Tasc", ctypes.c_void_p),
         ("rho_th", ctypes.c_double), ("tie_band", ctypes.c_double),
+        ("n_kap", ctypes.c_int), ("kap", ctypes.c_void_p), ("n_eta", ctypes.c_int), ("eta", ctypes.c_void_p),
     ]
 
 
@@ -84,6 +88,10 @@ def lib():
             L.orc_track_x.argtypes = [d, vp, vp, d, d, d, d]
             L.orc_track_bin.restype = i64
             L.orc_track_bin.argtypes = [d, vp, vp, d, d, d, d, d, vp]
+            L.orc_track_x_ell1.restype = d
+            L.orc_track_x_ell1.argtypes = [d, vp, vp, d, d, d, d, d, d]
+            L.orc_track_bin_ell1.restype = i64
+            L.orc_track_bin_ell1.argtypes = [d, vp, vp, d, d, d, d, d, d, d, vp]
             L.orc_count_one.restype = i
             L.orc_count_one.argtypes = [P, i, i64, i, vp, vp, vp, vp, vp, vp, vp]
             L.orc_count_dense.restype = i
@@ -175,13 +183,25 @@ def track_bin(F, v, n, ap, Om, Tasc, t, tie_band: float = TIE_BAND):
     return int(k), bool(tie.value)
 
 
+def track_x_ell1(F, v, n, ap, Om, Tasc, kap, eta, t) -> float:
+    v, n = _c(v, np.float64), _c(n, np.float64)
+    return lib().orc_track_x_ell1(F, _ptr(v), _ptr(n), ap, Om, Tasc, kap, eta, t)
+
+
+def track_bin_ell1(F, v, n, ap, Om, Tasc, kap, eta, t, tie_band: float = TIE_BAND):
+    v, n = _c(v, np.float64), _c(n, np.float64)
+    tie = ctypes.c_int()
+    k = lib().orc_track_bin_ell1(F, _ptr(v), _ptr(n), ap, Om, Tasc, kap, eta, t, tie_band, ctypes.byref(tie))
+    return int(k), bool(tie.value)
+
+
 # ----------------------------------------------------------------- counting
 
 class OracleProblem:
     """Holds contiguous arrays alive for the ctypes struct."""
 
     def __init__(self, *, bits, w, v, t, F0, n_f0, sky, a_p, Omega, T_asc, k_lo, K, rho=None,
-                 rho_th: float = 1.6, tie_band: float = TIE_BAND):
+                 rho_th: float = 1.6, tie_band: float = TIE_BAND, kappa=None, eta=None):
         self.bits = _c(bits, np.uint32)
         self.w = _c(w, np.float64)
         self.v = _c(v, np.float64)
@@ -193,7 +213,11 @@ class OracleProblem:
         self.rho = None if rho is None else _c(rho, np.float32)
         N, W = self.bits.shape
         self.n_T = self.Tasc.shape[1] if self.Tasc.ndim == 2 else self.Tasc.size // self.Om.size
-        self.B = self.ap.size * self.Om.size * self.n_T
+        self.kap = None if kappa is None else _c(kappa, np.float64)
+        self.eta = None if eta is None else _c(eta, np.float64)
+        nk = 1 if self.kap is None else self.kap.size
+        ne = 1 if self.eta is None else self.eta.size
+        self.B = self.ap.size * self.Om.size * self.n_T * nk * ne
         self.S = self.sky.shape[0]
         self.n_f0 = int(n_f0)
         self.N = N
@@ -203,7 +227,11 @@ class OracleProblem:
                          v=self.v.ctypes.data, t=self.t.ctypes.data, F0=float(F0), n_f0=self.n_f0,
                          S=self.S, sky=self.sky.ctypes.data, n_ap=self.ap.size, ap=self.ap.ctypes.data,
                          n_Om=self.Om.size, Om=self.Om.ctypes.data, n_T=self.n_T,
-                         Tasc=self.Tasc.ctypes.data, rho_th=float(rho_th), tie_band=float(tie_band))
+                         Tasc=self.Tasc.ctypes.data, rho_th=float(rho_th), tie_band=float(tie_band),
+                         n_kap=0 if self.kap is None else self.kap.size,
+                         kap=None if self.kap is None else self.kap.ctypes.data,
+                         n_eta=0 if self.eta is None else self.eta.size,
+                         eta=None if self.eta is None else self.eta.ctypes.data)
 
     def count_one(self, s: int, b: int, j: int):
         nu, nw, nt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()

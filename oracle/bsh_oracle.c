@@ -11,7 +11,8 @@
  *
  *   peakgram      Eq. (20)-(21) and the 1/0 threshold of Sec. IV.A
  *   weights       Eq. (22), antenna patterns of Eq. (1)
- *   track         Eq. (15) multiplied by T_c, rounded to the nearest bin
+ *   track         Eq. (15) multiplied by T_c, rounded to the nearest bin;
+ *                 Eq. (14) (ELL1, first order in e) for eccentric grids
  *   number count  Sec. IV.C: weighted sum of 1s and 0s along the track
  *   significance  Eq. (25)
  *   toplist       Sec. IV.C: per-region list ranked by s_H
@@ -212,10 +213,37 @@ int64_t orc_track_bin(double F, const double* v, const double* n, double ap, dou
     return (int64_t)floor(x + 0.5);
 }
 
+/* Low-eccentricity (ELL1) track, first order in e (Eq. (14), Sec. II):       */
+/*   f(t)T = F (1 + v.n - a_p Omega g),                                      */
+/*   g = cos(phi) + kappa cos(2 phi) + eta sin(2 phi),  phi = Omega (t - t_asc)  */
+/* with kappa = e cos(omega), eta = e sin(omega).  The sign of the eta term   */
+/* is the one the paper's exact Keplerian orbit (Eq. (6)-(10)) gives at       */
+/* first order in e; Eq. (14) as printed carries the opposite sign.  With    */
+/* kappa = eta = 0, g = cos(phi) exactly and the circular track is recovered */
+/* bit for bit.  Evaluation order: vn as above, phi = Omega (t - t_asc),     */
+/* g = (cos(phi) + kappa cos(2 phi)) + eta sin(2 phi), D = vn - a_p (Omega g). */
+double orc_track_x_ell1(double F, const double* v, const double* n, double ap, double Om,
+                        double Tasc, double kap, double eta, double t) {
+    double vn = (v[0] * n[0] + v[1] * n[1]) + v[2] * n[2];
+    double phi = Om * (t - Tasc);
+    double g = (cos(phi) + kap * cos(2.0 * phi)) + eta * sin(2.0 * phi);
+    double D = vn - ap * (Om * g);
+    return F + F * D;
+}
+
+int64_t orc_track_bin_ell1(double F, const double* v, const double* n, double ap, double Om,
+                           double Tasc, double kap, double eta, double t, double tie_band, int* tie) {
+    double x = orc_track_x_ell1(F, v, n, ap, Om, Tasc, kap, eta, t);
+    double fr = x - floor(x);
+    if (tie) *tie = fabs(fr - 0.5) < tie_band;
+    return (int64_t)floor(x + 0.5);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One band searched over a sky set and a binary grid.                      */
-/* Template order: id = ((s * B + b) * n_f0 + j),                           */
-/* b = (iOm * n_T + iT) * n_ap + iap, F_j = F0 + j.                         */
+/* Template order: id = ((s * B + b) * n_f0 + j), F_j = F0 + j,            */
+/* b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap.          */
+/* n_kap = n_eta = 0 means one value 0 each (circular orbits).              */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -238,16 +266,29 @@ typedef struct {
     const double* Tasc;    /* [n_Om][n_T] */
     double rho_th;
     double tie_band;
+    int n_kap;
+    const double* kap;    /* [n_kap] e cos(omega), or NULL with n_kap = 0 */
+    int n_eta;
+    const double* eta;    /* [n_eta] e sin(omega), or NULL with n_eta = 0 */
 } orc_problem;
 
-static void template_params(const orc_problem* pr, int64_t b, double* ap, double* Om, double* Ta) {
+static void template_params(const orc_problem* pr, int64_t b, double* ap, double* Om, double* Ta,
+                            double* kap, double* eta) {
+    int nk = pr->n_kap > 0 ? pr->n_kap : 1;
+    int ne = pr->n_eta > 0 ? pr->n_eta : 1;
     int64_t iap = b % pr->n_ap;
     int64_t r = b / pr->n_ap;
+    int64_t ie = r % ne;
+    r /= ne;
+    int64_t ik = r % nk;
+    r /= nk;
     int64_t iT = r % pr->n_T;
     int64_t iOm = r / pr->n_T;
     *ap = pr->ap[iap];
     *Om = pr->Om[iOm];
     *Ta = pr->Tasc[iOm * pr->n_T + iT];
+    *kap = pr->n_kap > 0 ? pr->kap[ik] : 0.0;
+    *eta = pr->n_eta > 0 ? pr->eta[ie] : 0.0;
 }
 
 /* Number count of one template (Sec. IV.C): n = sum_i w_i * bit_i[k_i].
@@ -257,15 +298,16 @@ static void template_params(const orc_problem* pr, int64_t b, double* ap, double
 int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
                   int32_t* n_unw, double* n_w, int32_t* n_tie,
                   int32_t* unw_lo, int32_t* unw_hi, double* w_lo, double* w_hi) {
-    double ap, Om, Ta;
-    template_params(pr, b, &ap, &Om, &Ta);
+    double ap, Om, Ta, kap, eta;
+    template_params(pr, b, &ap, &Om, &Ta, &kap, &eta);
     double F = pr->F0 + (double)j;
     const double* n = pr->sky + 3 * (size_t)s;
     int32_t cu = 0, ties = 0, lo = 0, hi = 0;
     double cw = 0.0, wl = 0.0, wh = 0.0;
     for (int i = 0; i < pr->N; ++i) {
         int tie;
-        int64_t k = orc_track_bin(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, pr->t[i], pr->tie_band, &tie);
+        int64_t k = orc_track_bin_ell1(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, kap, eta, pr->t[i],
+                                       pr->tie_band, &tie);
         int64_t col = k - pr->k_lo;
         if (col < 0 || col >= pr->K) return ORC_ERR_RANGE;
         const uint32_t* row = pr->bits + (size_t)i * pr->W;
@@ -275,7 +317,7 @@ int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
         if (bit) cw += wi;
         if (tie) {
             /* the other candidate bin: the neighbour on the far side of the half */
-            double x = orc_track_x(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, pr->t[i]);
+            double x = orc_track_x_ell1(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, kap, eta, pr->t[i]);
             int64_t alt = (x + 0.5 - floor(x + 0.5) < 0.5) ? k - 1 : k + 1;
             int64_t ca = alt - pr->k_lo;
             int abit = 0;
@@ -303,7 +345,8 @@ int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
 int orc_count_dense(const orc_problem* pr, int s_begin, int s_end,
                     int32_t* n_unw, double* n_w, int32_t* n_tie,
                     int32_t* unw_lo, int32_t* unw_hi, double* w_lo, double* w_hi) {
-    int64_t B = (int64_t)pr->n_ap * pr->n_Om * pr->n_T;
+    int64_t B = (int64_t)pr->n_ap * pr->n_Om * pr->n_T * (pr->n_kap > 0 ? pr->n_kap : 1) *
+                (pr->n_eta > 0 ? pr->n_eta : 1);
     size_t idx = 0;
     for (int s = s_begin; s < s_end; ++s)
         for (int64_t b = 0; b < B; ++b)
@@ -361,13 +404,13 @@ int64_t orc_topk(const double* scores, int64_t n, int64_t k, int64_t* out_ids, d
 /* ------------------------------------------------------------------------ */
 
 int orc_power_sum(const orc_problem* pr, int s, int64_t b, int j, double* P) {
-    double ap, Om, Ta;
-    template_params(pr, b, &ap, &Om, &Ta);
+    double ap, Om, Ta, kap, eta;
+    template_params(pr, b, &ap, &Om, &Ta, &kap, &eta);
     double F = pr->F0 + (double)j;
     const double* n = pr->sky + 3 * (size_t)s;
     double acc = 0.0;
     for (int i = 0; i < pr->N; ++i) {
-        int64_t k = orc_track_bin(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, pr->t[i], 0.0, 0);
+        int64_t k = orc_track_bin_ell1(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, kap, eta, pr->t[i], 0.0, 0);
         int64_t col = k - pr->k_lo;
         if (col < 0 || col >= pr->K) return ORC_ERR_RANGE;
         acc += pr->w[(size_t)s * pr->N + i] * (double)pr->rho[(size_t)i * pr->K + col];

@@ -166,6 +166,8 @@ class Problem:
     median_window: int       # 101, or 0 when ``power`` already holds rho
     rho_th: float = 1.6
     top_k: int = 1000
+    kappa: Optional[np.ndarray] = None   # [n_kap] e cos(omega) (Eq. (14)); None: circular orbits
+    eta: Optional[np.ndarray] = None     # [n_eta] e sin(omega)
 
     @property
     def N(self) -> int:
@@ -177,7 +179,9 @@ class Problem:
 
     @property
     def B(self) -> int:
-        return int(self.a_p.size * self.T_asc.size)
+        nk = 1 if self.kappa is None else int(np.size(self.kappa))
+        ne = 1 if self.eta is None else int(np.size(self.eta))
+        return int(self.a_p.size * self.T_asc.size * nk * ne)
 
     @property
     def n_templates(self) -> int:
@@ -189,13 +193,14 @@ class Problem:
 
 
 def band_for(F_min: float, F_max: float, v_max: float, ap_max: float, Om_max: float,
-             min_K: int = 0):
+             min_K: int = 0, ecc_max: float = 0.0):
     """Loaded band [k_lo, k_lo+K) covering every track, plus words per row.
 
-    The margin bounds |F*(v.n - a_p*Omega*cos)| + 2 bins; K is widened to at
-    least ``min_K`` (the running-median window) and W padded to 4 words.
+    The margin bounds |F*(v.n - a_p*Omega*g)| + 2 bins with |g| <= 1 + ecc_max
+    (ecc_max = max|kappa| + max|eta|); K is widened to at least ``min_K`` (the
+    running-median window) and W padded to 4 words.
     """
-    margin = int(math.ceil(F_max * (v_max + ap_max * Om_max))) + 2
+    margin = int(math.ceil(F_max * (v_max + ap_max * Om_max * (1.0 + ecc_max)))) + 2
     k_lo = int(math.floor(F_min)) - margin
     k_hi = int(math.floor(F_max)) + 1 + margin
     K = k_hi - k_lo + 1
@@ -224,7 +229,8 @@ def make_problem(name: str, *, n_per_det: int, dets: List[str], T_sft: float, sp
                  sky: np.ndarray, patch_size: int, a_p: np.ndarray, P_days: np.ndarray,
                  n_T: int, power_kind: str, seed: int = SEED_NOISE, top_k: int = 1000,
                  orbit_only: bool = False, sn_ratio: Optional[float] = None,
-                 patch_start: Optional[np.ndarray] = None) -> Problem:
+                 patch_start: Optional[np.ndarray] = None, kappa: Optional[np.ndarray] = None,
+                 eta: Optional[np.ndarray] = None) -> Problem:
     rng = np.random.default_rng(seed)
     ts, vs, arms, Sns, detidx = [], [], [], [], []
     if sn_ratio is None:
@@ -245,8 +251,10 @@ def make_problem(name: str, *, n_per_det: int, dets: List[str], T_sft: float, sp
     T_asc = _tasc_grid(Omega, n_T)
     F0 = math.floor(f_lo * T_sft) + (0.5 if half_bin else 0.0)
     v_max = float(np.max(np.linalg.norm(v, axis=1)))
+    ecc_max = (0.0 if kappa is None else float(np.max(np.abs(kappa)))) + \
+        (0.0 if eta is None else float(np.max(np.abs(eta))))
     k_lo, K, W = band_for(F0, F0 + n_f0 - 1, v_max, float(np.max(a_p)), float(np.max(Omega)),
-                          min_K=101 if power_kind == "gauss" else 0)
+                          min_K=101 if power_kind == "gauss" else 0, ecc_max=ecc_max)
     prng = np.random.default_rng(seed + 17)
     if power_kind == "exp":
         power = exp_rho(t.size, K, prng)
@@ -261,7 +269,9 @@ def make_problem(name: str, *, n_per_det: int, dets: List[str], T_sft: float, sp
     return Problem(name=name, T_sft=T_sft, t=t, v=v, arms=arm, Sn=Sn, det=det, sky=sky,
                    patch_start=np.asarray(patch_start, dtype=np.int64), a_p=np.asarray(a_p, dtype=np.float64),
                    Omega=Omega, T_asc=T_asc, F0=float(F0), n_f0=int(n_f0), k_lo=k_lo, K=K, W=W,
-                   power=power, median_window=mw, top_k=top_k)
+                   power=power, median_window=mw, top_k=top_k,
+                   kappa=None if kappa is None else np.asarray(kappa, dtype=np.float64),
+                   eta=None if eta is None else np.asarray(eta, dtype=np.float64))
 
 
 def tiny(seed: int = SEED_NOISE) -> Problem:
@@ -296,6 +306,21 @@ def mid(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,
                         n_T=n_T, power_kind="gauss", seed=seed, top_k=top_k, orbit_only=orbit_only)
 
 
+def eccentric(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 16, n_P: int = 16, n_T: int = 16,
+              n_kap: int = 3, n_eta: int = 3, e_max: float = 0.02, seed: int = SEED_NOISE,
+              patch_size: int = 50, top_k: int = 1000) -> Problem:
+    """Low-eccentricity search (Eq. (14)): the mid construction (2 x 2000 SFTs over 1 yr,
+    200 Hz, patches of 50) with a 16^3 circular grid widened by kappa, eta in
+    [-e_max, e_max] (3 x 3), so B = 16^3 * 9 = 36864 binary templates."""
+    sky = fibonacci_sky(n_sky)
+    return make_problem("eccentric", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=900.0, span=YEAR_SID,
+                        random_times=True, f_lo=200.0, n_f0=90, half_bin=False, sky=sky,
+                        patch_size=patch_size, a_p=np.linspace(0.5, 10.0, n_ap),
+                        P_days=np.linspace(15.0, 45.0, n_P), n_T=n_T, power_kind="gauss", seed=seed,
+                        top_k=top_k, kappa=np.linspace(-e_max, e_max, n_kap),
+                        eta=np.linspace(-e_max, e_max, n_eta))
+
+
 def precision_stress(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,
                      n_T: int = 32, seed: int = SEED_NOISE) -> Problem:
     """Mid workload on the half-bin f0 grid (F = k + 1/2), detector velocities
@@ -309,7 +334,7 @@ def precision_stress(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n
 
 
 def batching(n_patch: int = 64, size_lo: int = 500, size_hi: int = 5000, n_per_det: int = 500,
-             seed: int = SEED_NOISE, n_bin: int = 8) -> List[Problem]:
+             seed: int = SEED_NOISE, n_bin: int = 8, power_kind: str = "gauss") -> List[Problem]:
     """Batching: 64 sky patches of uneven size (500-5000 points, seeded) searched
     in four 1 Hz bands at 100/200/300/400 Hz with T_c = 900/600/450/360 s;
     2 x 500 SFTs over 30 days per band; 8 x 8 x 8 binary grid."""
@@ -322,17 +347,17 @@ def batching(n_patch: int = 64, size_lo: int = 500, size_hi: int = 5000, n_per_d
         out.append(make_problem(f"batch{int(f)}", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=T,
                                 span=30 * DAY, random_times=True, f_lo=f, n_f0=int(round(T)),
                                 half_bin=False, sky=sky, patch_size=0, a_p=np.linspace(0.5, 5.0, n_bin),
-                                P_days=np.linspace(15.0, 45.0, n_bin), n_T=n_bin, power_kind="gauss",
+                                P_days=np.linspace(15.0, 45.0, n_bin), n_T=n_bin, power_kind=power_kind,
                                 seed=seed + int(f), top_k=1000, patch_start=ps))
     return out
 
 
 def full(n_sky: int = 100048, n_per_det: int = 4000, n_f0: int = 9000, seed: int = SEED_NOISE,
-         patch_size: int = 169) -> Problem:
+         patch_size: int = 169, power_kind: str = "gauss") -> Problem:
     """Full scale: 2 x 4000 SFTs over 1 yr, 10 Hz band at 300 Hz, ~1e5 sky points
     in patches of 169, a_p 0.5-15 ls, P 10-60 d (8 x 8 x 8), top-10000."""
     return make_problem("full", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=900.0, span=YEAR_SID,
                         random_times=True, f_lo=300.0, n_f0=n_f0, half_bin=False,
                         sky=fibonacci_sky(n_sky), patch_size=patch_size,
                         a_p=np.linspace(0.5, 15.0, 8), P_days=np.linspace(10.0, 60.0, 8), n_T=8,
-                        power_kind="gauss", seed=seed, top_k=10000)
+                        power_kind=power_kind, seed=seed, top_k=10000)

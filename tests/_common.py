@@ -23,7 +23,7 @@ def oracle_inputs(pr, dtype="f64"):
 def oracle_problem(pr, bits, w, rho=None):
     return oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky,
                                 a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K,
-                                rho=rho, rho_th=pr.rho_th)
+                                rho=rho, rho_th=pr.rho_th, kappa=pr.kappa, eta=pr.eta)
 
 
 def pack_bits(on, W):
@@ -35,21 +35,37 @@ def pack_bits(on, W):
     return out
 
 
-def template_of(pr, b):
+def orbit_of(pr, b):
+    """(a_p, Omega, t_asc, kappa, eta) of binary index b:
+    b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap."""
+    nk = 1 if pr.kappa is None else pr.kappa.size
+    ne = 1 if pr.eta is None else pr.eta.size
     iap = b % pr.a_p.size
     r = b // pr.a_p.size
+    ie = r % ne
+    r //= ne
+    ik = r % nk
+    r //= nk
     iT = r % pr.T_asc.shape[1]
     iOm = r // pr.T_asc.shape[1]
-    return pr.a_p[iap], pr.Omega[iOm], pr.T_asc[iOm, iT]
+    kap = 0.0 if pr.kappa is None else float(pr.kappa[ik])
+    eta = 0.0 if pr.eta is None else float(pr.eta[ie])
+    return pr.a_p[iap], pr.Omega[iOm], pr.T_asc[iOm, iT], kap, eta
+
+
+def template_of(pr, b):
+    """(a_p, Omega, t_asc) of binary index b of a circular-orbit problem."""
+    assert pr.kappa is None and pr.eta is None
+    return orbit_of(pr, b)[:3]
 
 
 def track_bins(pr, s, b, j):
     """Oracle bins (and tie flags) of one template in every SFT."""
-    ap, Om, Ta = template_of(pr, b)
+    ap, Om, Ta, kap, eta = orbit_of(pr, b)
     F = pr.F0 + j
     ks, ties = [], []
     for i in range(pr.N):
-        k, t = oracle.track_bin(F, pr.v[i], pr.sky[s], ap, Om, Ta, pr.t[i])
+        k, t = oracle.track_bin_ell1(F, pr.v[i], pr.sky[s], ap, Om, Ta, kap, eta, pr.t[i])
         ks.append(k)
         ties.append(t)
     return np.array(ks), np.array(ties)

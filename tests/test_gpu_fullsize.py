@@ -88,3 +88,69 @@ def test_random_templates_respect_the_kth_score(run):
                 continue
             _, sH = _score(op, wq, s, b, j)
             assert sH <= kth + 2e-4, (p, s, b, j, sH, kth)
+
+
+def _sampled_check(pr, op, wq, lists, first_region, rng, n_patch_check=2, n_entries=25, n_random=100):
+    per_s = pr.B * pr.n_f0
+    n_patch = len(pr.patch_start) - 1
+    for p in rng.choice(n_patch, min(n_patch_check, n_patch), replace=False):
+        g = lists[first_region + p]
+        s0, s1 = pr.patch_start[p], pr.patch_start[p + 1]
+        assert g.size == min(pr.top_k, (s1 - s0) * per_s)
+        assert np.all(np.diff(g["s_h"]) <= 0)
+        for e in list(range(5)) + list(rng.choice(np.arange(5, g.size), n_entries - 5, replace=False)):
+            c = g[e]
+            s, rem = divmod(int(c["template_id"]), per_s)
+            b, j = divmod(rem, pr.n_f0)
+            assert s0 <= s < s1
+            ref, sH = _score(op, wq, s, b, j)
+            assert ref["unw_lo"] <= int(c["n_unw"]) <= ref["unw_hi"]
+            assert abs(float(c["n_w"]) - ref["n_w"]) <= REL_TOL * ref["n_w"]
+            assert abs(float(c["s_h"]) - sH) < 2e-4
+            P = op.power_sum(s, b, j)
+            assert abs(float(c["power"]) - P) <= REL_TOL * P
+        kth = float(g["s_h"][-1])
+        ids = set(int(x) for x in g["template_id"])
+        for _ in range(n_random):
+            s = int(rng.integers(s0, s1))
+            b = int(rng.integers(pr.B))
+            j = int(rng.integers(pr.n_f0))
+            if (s * pr.B + b) * pr.n_f0 + j in ids:
+                continue
+            _, sH = _score(op, wq, s, b, j)
+            assert sH <= kth + 2e-4
+
+
+def test_full_scale_shape_with_stage2():
+    # config-5 shape: 2 x 4000 SFTs over 1 yr, 9000 f0 bins at 300 Hz, 8^3 binaries, patches of
+    # 169 sky points, top-10000, stage-2 power sums; 6 patches of the sky (rho given directly)
+    pr = synth.full(n_sky=1014, power_kind="exp")
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    plan.autotune()
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(1000)
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    plan.close()
+    _sampled_check(pr, op, wq, lists, 0, np.random.default_rng(11))
+
+
+def test_batching_shape_multi_band():
+    # config-3 shape: four 1 Hz bands (T_c = 900/600/450/360 s), 2 x 500 SFTs each, 8^3 binaries,
+    # uneven patches; one persistent launch over all bands
+    probs = synth.batching(n_patch=4, size_lo=20, size_hi=60, power_kind="exp")
+    dps = [device_problem(p, "f16") for p in probs]
+    plan = bsh.Plan([d[0] for d in dps], bsh.MODE_BATCHED, top_k=1000)
+    plan.autotune()
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(100)
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    rng = np.random.default_rng(12)
+    for q, (dp, op, wq) in enumerate(dps):
+        _sampled_check(dp.pr, op, wq, lists, plan.first_region(q), rng, n_patch_check=1, n_entries=15,
+                       n_random=40)
+    plan.close()
