@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "small"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "small", "eccentric"], default="mid")
     ap.add_argument("--graph", action="store_true", help="replay count+toplist+power as one CUDA graph")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -52,14 +52,22 @@ def parse():
 
 def make_problem(kind: str, rank: int):
     from paper_1904_04873_gb300 import synth
-    if kind == "mid":
-        sky = synth.fibonacci_sky(2000)
-    else:
-        sky = synth.fibonacci_sky(200)
-    sky = rank_sky(sky, rank)
+    sky = rank_sky(synth.fibonacci_sky(200 if kind == "small" else 2000), rank)
     if kind == "mid":
         return synth.mid(sky=sky)
+    if kind == "eccentric":
+        return synth.eccentric(sky=sky)
     return synth.mid(n_sky=200, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky)
+
+
+def plain_sample(kind: str, sky: np.ndarray):
+    """The first 4 sky points of the workload, for the plain-form sample."""
+    from paper_1904_04873_gb300 import synth
+    if kind == "mid":
+        return synth.mid(sky=sky[:4], patch_size=50)
+    if kind == "eccentric":
+        return synth.eccentric(sky=sky[:4])
+    return synth.mid(n_sky=4, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky[:4])
 
 
 def rank_sky(sky: np.ndarray, rank: int) -> np.ndarray:
@@ -94,9 +102,12 @@ def weak_value(terms_per_rank: float, world: int, t_max: float) -> float:
 
 
 def workload_config(pr, kind):
+    binary = f"{pr.a_p.size}x{pr.Omega.size}x{pr.T_asc.shape[1]}"
+    if pr.kappa is not None:
+        binary += (f"x{pr.kappa.size}x{pr.eta.size} ELL1 (kappa, eta in +-{float(np.max(np.abs(pr.kappa))):g})")
     return {"workload": f"{kind}: {pr.N} SFTs (2 det, T_c=900 s, 1 yr), band {pr.F0 / 900.0:.1f}-"
                         f"{(pr.F0 + pr.n_f0) / 900.0:.1f} Hz, {pr.S} sky pts in patches of 50, "
-                        f"{pr.a_p.size}x{pr.Omega.size}x{pr.T_asc.shape[1]} binary, {pr.n_f0} f0, top-{pr.top_k}",
+                        f"{binary} binary, {pr.n_f0} f0, top-{pr.top_k}",
             "templates": int(pr.n_templates), "terms_per_step": int(pr.n_terms), "weights": "fp16",
             "l2": "256 MiB L2 flush write between steps"}
 
@@ -185,13 +196,13 @@ def measured_peaks():
 
 def _oracle_worker(args):
     """Spawned process: time the oracle on binary templates [b0, b1) of sky point 0."""
-    (bits, w, v, t, F0, n_f0, sky, a_p, Om, Ta, k_lo, K, b0, b1) = args
+    (bits, w, v, t, F0, n_f0, sky, a_p, Om, Ta, kap, eta, k_lo, K, b0, b1) = args
     import sys
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
     import oracle
     op = oracle.OracleProblem(bits=bits, w=w, v=v, t=t, F0=F0, n_f0=n_f0, sky=sky, a_p=a_p, Omega=Om,
-                              T_asc=Ta, k_lo=k_lo, K=K)
+                              T_asc=Ta, k_lo=k_lo, K=K, kappa=kap, eta=eta)
     t0 = time.perf_counter()
     for b in range(b0, b1):
         for j in range(n_f0):
@@ -208,7 +219,8 @@ def cpu_baseline_sample(pr, budget_s: float = 12.0, procs: int = 0):
     procs = procs or (os.cpu_count() or 1)
     rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
     w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.k_lo, pr.K)
+    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.kappa, pr.eta,
+            pr.k_lo, pr.K)
     per_b = _oracle_worker(base + (0, 2)) / 2          # calibration, in this process
     nb = max(1, min(pr.B // procs, int(budget_s / max(per_b, 1e-6))))
     ctx = mp.get_context("spawn")
@@ -233,7 +245,8 @@ def run_reference(args):
     procs = os.cpu_count() or 1
     rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
     w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.k_lo, pr.K)
+    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.kappa, pr.eta,
+            pr.k_lo, pr.K)
     per_b = _oracle_worker(base + (0, 1))
     nb = max(1, min(pr.B // (procs * max(1, args.steps + args.warmup)), int(1.5 / max(per_b, 1e-6))))
 
@@ -383,9 +396,7 @@ def main():
     # ---- plain form (FP64 track per term, FP64 weights, one launch per patch) on a bounded sample
     plain = None
     if not args.no_plain and rank == 0:
-        from paper_1904_04873_gb300 import synth
-        sub = synth.mid(sky=pr.sky[:4], patch_size=50) if args.workload == "mid" else \
-            synth.mid(n_sky=4, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=pr.sky[:4])
+        sub = plain_sample(args.workload, pr.sky)
         dps = bsh.DeviceProblem(sub, w_dtype="f64")
         dps.prepare()
         pplan = bsh.Plan([dps], bsh.MODE_PLAIN, top_k=pr.top_k)

@@ -23,8 +23,18 @@
  *     or prints.
  *   - Row-major layouts: [a][b] means b is the fastest index.
  *   - Frequencies are bin numbers F = f * T_c (Eq. (33): delta f = 1/T_c).
- *   - Template order inside a problem: id = ((s * B + b) * n_f0 + j) with the
- *     binary index b = (iOm * n_T + iT) * n_ap + iap and F_j = F0 + j.
+ *   - Template order inside a problem: id = ((s * B + b) * n_f0 + j) with
+ *     F_j = F0 + j and the binary index
+ *       b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap,
+ *     where n_kap (n_eta) counts as 1 when the problem gives no kappa (eta).
+ *   - Track of a template at SFT i (Eq. (14) and (15) times T_c):
+ *       k_i = floor(F (1 + v_i.n - a_p Omega g_i) + 1/2),
+ *       g_i = cos(phi) + kappa cos(2 phi) + eta sin(2 phi),
+ *       phi = Omega (t_i - t_asc),  kappa = e cos(omega),  eta = e sin(omega),
+ *     the low-eccentricity (ELL1) expansion to first order in e; kappa =
+ *     eta = 0 is the circular orbit of Eq. (15).  The sign of the eta term
+ *     is the one that the exact Keplerian orbit of Eq. (6)-(10) gives at first
+ *     order in e (Eq. (11) and (14) print the opposite sign).
  */
 #ifndef BSH_H
 #define BSH_H
@@ -112,7 +122,9 @@ int bsh_weights(const double* sky, int S, const double* arms, const double* Sn, 
 
 /* ------------------------------------------------------------------------ */
 /* Search problem: one loaded frequency band, a sky set split into patches   */
-/* and a circular-orbit binary grid (Sec. V.A-V.B).                           */
+/* and a binary grid (Sec. V.A-V.B): circular orbits (a_p, Omega, t_asc), or */
+/* low-eccentricity orbits with the two extra ELL1 parameters of Eq. (14).   */
+/* A zero-initialised tail (n_kappa = n_eta = 0) means circular orbits.      */
 /* ------------------------------------------------------------------------ */
 typedef struct bsh_problem {
     /* band */
@@ -145,6 +157,11 @@ typedef struct bsh_problem {
     int n_T;
     const double* T_asc;       /* [n_Om][n_T] time of ascension (s), Eq. (35) range */
     double rho_th;             /* peak threshold used for the peakgram (1.6), Eq. (25) mean */
+    /* eccentric grid, HOST arrays (copied by bsh_plan_create); 0 / NULL = none */
+    int n_kappa;
+    const double* kappa;       /* [n_kappa] e cos(omega), |kappa| <= 0.5 */
+    int n_eta;
+    const double* eta;         /* [n_eta] e sin(omega), |eta| <= 0.5 */
 } bsh_problem;
 
 typedef struct bsh_count_options {
@@ -205,7 +222,7 @@ int bsh_plan_accumulate(const bsh_plan* plan);
 /* ------------------------------------------------------------------------ */
 /* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */
 /* sum n = sum_i w_i * bit_i[k_i] along the track k_i = round(f(t_i) T_c) of  */
-/* Eq. (15), its significance s_H of Eq. (25), and a fused per-patch         */
+/* Eq. (14)/(15), its significance s_H of Eq. (25), and a fused per-patch    */
 /* toplist of the top_k largest s_H (ties: smaller template id first).       */
 /* Reads the problems' bits, w, sums, v, t and sky arrays.  Capturable.      */
 /* ------------------------------------------------------------------------ */
@@ -257,7 +274,7 @@ int bsh_graph_launch(bsh_plan* plan, bsh_cand* cands, int32_t* n_cands, int n_cf
 int bsh_graph_reset(bsh_plan* plan);
 
 /* ------------------------------------------------------------------------ */
-/* Track diagnostics, Eq. (15).                                              */
+/* Track diagnostics, Eq. (14)/(15).                                         */
 /* bsh_track_precision: for every term of sky points [s_begin, s_end) of the */
 /* plan's problem (every binary template, SFT and f0 template) compares the  */
 /* exact FP64 bin with (a) the same expression evaluated in single          */

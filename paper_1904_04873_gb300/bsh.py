@@ -45,7 +45,22 @@ class Problem(ctypes.Structure):
         ("n_Om", ctypes.c_int), ("Omega", ctypes.c_void_p),
         ("n_T", ctypes.c_int), ("T_asc", ctypes.c_void_p),
         ("rho_th", ctypes.c_double),
+        ("n_kappa", ctypes.c_int), ("kappa", ctypes.c_void_p),
+        ("n_eta", ctypes.c_int), ("eta", ctypes.c_void_p),
     ]
+
+
+def _ecc_fields(pr, keep: dict) -> dict:
+    """n_kappa / kappa / n_eta / eta of a problem (HOST arrays kept alive in ``keep``)."""
+    out = {}
+    for name in ("kappa", "eta"):
+        a = getattr(pr, name, None)
+        if a is None:
+            out["n_" + name], out[name] = 0, None
+        else:
+            keep[name] = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            out["n_" + name], out[name] = keep[name].size, keep[name].ctypes.data
+    return out
 
 
 class CountOptions(ctypes.Structure):
@@ -215,6 +230,8 @@ class DeviceProblem:
         self._ap = np.ascontiguousarray(pr.a_p, dtype=np.float64)
         self._Om = np.ascontiguousarray(pr.Omega, dtype=np.float64)
         self._Ta = np.ascontiguousarray(pr.T_asc, dtype=np.float64)
+        self._ecc = {}
+        ecc = _ecc_fields(pr, self._ecc)
         return Problem(N=pr.N, k_lo=pr.k_lo, K=pr.K, W=pr.W, bits=_ptr(self.bits), rho=_ptr(self.rho),
                        w=_ptr(self.w), w_dtype=DTYPE_CODES[self.w_dtype], sum_w=_ptr(self.sum_w),
                        sum_w2=_ptr(self.sum_w2), v=_ptr(self.v), t=_ptr(self.t), v_max=self.v_max,
@@ -222,7 +239,7 @@ class DeviceProblem:
                        n_patch=len(self._ps) - 1, patch_start=self._ps.ctypes.data,
                        n_ap=self._ap.size, a_p=self._ap.ctypes.data, n_Om=self._Om.size,
                        Omega=self._Om.ctypes.data, n_T=self._Ta.shape[1], T_asc=self._Ta.ctypes.data,
-                       rho_th=float(pr.rho_th))
+                       rho_th=float(pr.rho_th), **ecc)
 
 
 class Plan:
@@ -374,7 +391,7 @@ def debug_track_windows(pr, queries: np.ndarray, rows: np.ndarray):
                 v_max=v_max, F0=float(pr.F0), n_f0=pr.n_f0, S=pr.S, sky=arrs["sky"].ctypes.data, n_patch=1,
                 n_ap=arrs["ap"].size, a_p=arrs["ap"].ctypes.data, n_Om=arrs["Om"].size,
                 Omega=arrs["Om"].ctypes.data, n_T=arrs["Ta"].shape[1], T_asc=arrs["Ta"].ctypes.data,
-                rho_th=float(pr.rho_th))
+                rho_th=float(pr.rho_th), **_ecc_fields(pr, arrs))
     _check(lib().bsh_debug_track_windows(ctypes.byref(d), q.ctypes.data, n, rows.ctypes.data, out.ctypes.data,
                                          path.ctypes.data), "bsh_debug_track_windows")
     return out, path

@@ -1,14 +1,16 @@
 // Internal declarations shared by the CUDA translation units of libbsh.
 //
-// Track arithmetic (Eq. (15) times T_c):
-//   k_i(j) = floor(F_j + F_j * D_i + 1/2),  D_i = v_i.n - a_p * Omega * cos(Omega (t_i - t_asc))
+// Track arithmetic (Eq. (14)/(15) times T_c):
+//   k_i(j) = floor(F_j + F_j * D_i + 1/2),  D_i = v_i.n - a_p * (Omega * g_i),
+//   g_i = (cos(phi) + kappa cos(2 phi)) + eta sin(2 phi),  phi = Omega (t_i - t_asc)
+// (kappa = eta = 0: circular orbit, g_i = cos(phi)).
 // The hot kernels evaluate it in 32-bit fixed point, with a rigorous error
 // bound eps, and fall back to the exact FP64 expression whenever the fixed-point
 // value lies within M > eps of a rounding boundary.  The fixed-point value of
 //   v(j) = F_j * D + frac(F_j) + 1/2        (units of bins, scale 2^s_y)
 // is Z(j) - mulhi(ap_q, C_q(j)) with
 //   Z(j)   = round(F_j * vn * 2^s_y) + (frac(F_j) + 1/2) 2^s_y    from vn_q = round(vn 2^s_vn)
-//   C_q(j) = round(F_j * c * 2^s_C)                               from c_q  = round(c 2^s_c), c = Omega cos(..)
+//   C_q(j) = round(F_j * c * 2^s_C)                               from c_q  = round(c 2^s_c), c = Omega g
 //   ap_q   = round(a_p 2^s_a),  s_y = s_a + s_C - 32
 // and the bin is floor(F_j) + floor(v(j) / 2^s_y).  Since v is linear in j, a
 // block of 32 consecutive f0 templates needs v only at j0 and j0 + 31.
@@ -67,7 +69,7 @@ struct ProbDev {
     const double* sky;        // [S][3]
     // workspace tables
     int32_t* vn_q;            // [S][Np]
-    int32_t* c_q;             // [nOT][Np]
+    int32_t* c_q;             // [nOT][Np]   one row per orbit (Omega, t_asc, kappa, eta)
     double* c64;              // [nOT][Np]
     float* w32;               // [S][Np]   (batched mode)
     double* w64;              // [S][Np]   (plain mode)
@@ -75,10 +77,13 @@ struct ProbDev {
     const int32_t* ap_q;      // [n_ap]
     const double* Om;         // [n_Om]
     const double* Tasc;       // [n_Om * n_T]
+    const double* kap;        // [n_kap] or NULL (circular)
+    const double* eta;        // [n_eta] or NULL (circular)
     const int64_t* patch_start;  // [n_patch + 1]
     const int32_t* patch_of_s;   // [S]
     // sizes
     int N, Np, K, W, k_lo, n_f0, S, n_ap, n_Om, n_T, nOT, B, n_patch, w_dtype;
+    int n_kap, n_eta;         // >= 1 (1 with a NULL array: the value 0)
     double F0;                // first template (bins)
     int G0;                   // floor(F0)
     int JB;                   // valid templates per f0 block (<= 32)

@@ -55,6 +55,7 @@ int ceil_log2(double x) {
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 // Fixed-point scales for the track of one problem (see bsh_internal.cuh).
+// Om_max bounds |c| = |Omega g| over every orbit row (Omega (1 + |kappa| + |eta|)).
 int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max, double phi, FixedPoint* fp) {
     const double ymax = F_max * (v_max + ap_max * Om_max) + 2.0;
     fp->s_vn = 30 - ceil_log2(v_max * (1.0 + 1e-9));
@@ -75,7 +76,7 @@ int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max,
     const double ea = 0.5;
     const double prod = (ap_max * std::ldexp(1.0, fp->s_a) * eC + C_max * std::ldexp(1.0, fp->s_C) * ea + ea * eC) /
                         4294967296.0;
-    const double cosulp = F_max * Om_max * ap_max * 4.0e-16 * u;   // libm-level differences of cos
+    const double cosulp = F_max * Om_max * ap_max * 4.0e-16 * u;   // libm-level differences of cos / sin
     fp->eps = eZ + 1.0 + prod + cosulp + 1.0;
     fp->M = (int)std::ceil(2.0 * fp->eps) + 4;
     if (fp->M * 8 > (1 << fp->s_y)) return BSH_ERR_RANGE;
@@ -84,12 +85,44 @@ int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max,
 
 struct ProbHost {
     bsh_problem d;                         // caller descriptor (device pointers)
-    std::vector<double> ap, Om, Tasc;
+    std::vector<double> ap, Om, Tasc, kap, eta;   // kap / eta empty: circular orbits
     std::vector<int64_t> ps;
     std::vector<int32_t> patch_of_s, ap_q;
     ProbDev pd;                            // filled at create (sizes) and bind (pointers)
-    size_t off_ap, off_apq, off_Om, off_Tasc, off_ps, off_pos, off_vnq, off_cq, off_c64, off_w;
+    size_t off_ap, off_apq, off_Om, off_Tasc, off_kap, off_eta, off_ps, off_pos, off_vnq, off_cq, off_c64, off_w;
 };
+
+// Orbit rows of a problem: (Omega, t_asc) pairs times the eccentric grid.
+long long orbit_rows(const bsh_problem& d) {
+    return (long long)d.n_Om * d.n_T * std::max(1, d.n_kappa) * std::max(1, d.n_eta);
+}
+
+// Largest |kappa| and |eta| of the grid (0 when absent).
+double ecc_bound(const bsh_problem& d) {
+    double km = 0.0, em = 0.0;
+    for (int k = 0; k < d.n_kappa; ++k) km = std::max(km, std::fabs(d.kappa[k]));
+    for (int k = 0; k < d.n_eta; ++k) em = std::max(em, std::fabs(d.eta[k]));
+    return km + em;
+}
+
+void copy_grid(ProbHost& h, const bsh_problem& d) {
+    h.ap.assign(d.a_p, d.a_p + d.n_ap);
+    h.Om.assign(d.Omega, d.Omega + d.n_Om);
+    h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
+    if (d.n_kappa > 0) h.kap.assign(d.kappa, d.kappa + d.n_kappa);
+    else h.kap.clear();
+    if (d.n_eta > 0) h.eta.assign(d.eta, d.eta + d.n_eta);
+    else h.eta.clear();
+}
+
+// |Omega g| bound over the orbit rows, g of Eq. (14).
+double c_bound(const ProbHost& h) {
+    double Om_max = 0.0, km = 0.0, em = 0.0;
+    for (double o : h.Om) Om_max = std::max(Om_max, o);
+    for (double k : h.kap) km = std::max(km, std::fabs(k));
+    for (double e : h.eta) em = std::max(em, std::fabs(e));
+    return Om_max * (1.0 + km + em);
+}
 
 }  // namespace
 
@@ -162,6 +195,12 @@ int validate_problem(const bsh_problem& d) {
         if (!finite_pos(d.Omega[k])) return BSH_ERR_ARG;
     for (int k = 0; k < d.n_Om * d.n_T; ++k)
         if (!std::isfinite(d.T_asc[k])) return BSH_ERR_ARG;
+    if (d.n_kappa < 0 || d.n_eta < 0 || (d.n_kappa > 0 && !d.kappa) || (d.n_eta > 0 && !d.eta))
+        return BSH_ERR_ARG;
+    for (int k = 0; k < d.n_kappa; ++k)
+        if (!(std::fabs(d.kappa[k]) <= 0.5)) return BSH_ERR_ARG;
+    for (int k = 0; k < d.n_eta; ++k)
+        if (!(std::fabs(d.eta[k]) <= 0.5)) return BSH_ERR_ARG;
     return BSH_OK;
 }
 
@@ -178,9 +217,12 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
     pd.n_ap = d.n_ap;
     pd.n_Om = d.n_Om;
     pd.n_T = d.n_T;
-    pd.nOT = d.n_Om * d.n_T;
-    const long long B = (long long)d.n_ap * pd.nOT;
+    pd.n_kap = std::max(1, (int)h.kap.size());
+    pd.n_eta = std::max(1, (int)h.eta.size());
+    const long long rows = (long long)d.n_Om * d.n_T * pd.n_kap * pd.n_eta;
+    const long long B = (long long)d.n_ap * rows;
     if (B > (1LL << 30)) return BSH_ERR_RANGE;
+    pd.nOT = (int)rows;
     pd.B = (int)B;
     pd.n_patch = d.n_patch;
     pd.w_dtype = d.w_dtype;
@@ -197,9 +239,9 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
         const double nt = (double)(h.ps[q + 1] - h.ps[q]) * (double)B * d.n_f0;
         if (nt >= 4294967295.0) return BSH_ERR_RANGE;
     }
-    double ap_max = 0.0, Om_max = 0.0;
+    double ap_max = 0.0;
     for (double a : h.ap) ap_max = std::max(ap_max, a);
-    for (double o : h.Om) Om_max = std::max(Om_max, o);
+    const double Om_max = c_bound(h);
     const int j_last = (pd.n_fb - 1) * pd.JB + JW;             // last f0 offset evaluated (+1 for a crossing)
     const double F_eval = d.F0 + j_last;
     const double phi = d.F0 - std::floor(d.F0);
@@ -322,13 +364,13 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
         ProbHost& h = p->P[q];
         h.d = problems[q];
         const bsh_problem& d = problems[q];
-        h.ap.assign(d.a_p, d.a_p + d.n_ap);
-        h.Om.assign(d.Omega, d.Omega + d.n_Om);
-        h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
+        copy_grid(h, d);
         h.ps.assign(d.patch_start, d.patch_start + d.n_patch + 1);
         h.d.a_p = nullptr;
         h.d.Omega = nullptr;
         h.d.T_asc = nullptr;
+        h.d.kappa = nullptr;
+        h.d.eta = nullptr;
         h.d.patch_start = nullptr;
     }
     // size the workspace for every tile shape the autotuner may pick
@@ -381,9 +423,10 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     p->ot_max = 1;
     p->wrows = 1;
     for (auto& h : p->P) {
-        const int rows = std::min(h.d.n_Om * h.d.n_T, (p->threads + h.d.n_ap - 1) / h.d.n_ap + 1);
+        const long long nOT = orbit_rows(h.d);
+        const int rows = (int)std::min(nOT, (long long)((p->threads + h.d.n_ap - 1) / h.d.n_ap + 1));
         p->ot_max = std::max(p->ot_max, rows);
-        const int wr = std::min(h.d.n_Om * h.d.n_T, (32 + h.d.n_ap - 1) / h.d.n_ap + 1);
+        const int wr = (int)std::min(nOT, (long long)((32 + h.d.n_ap - 1) / h.d.n_ap + 1));
         p->wrows = std::max(p->wrows, wr);
     }
     int region = 0;
@@ -521,7 +564,9 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         h.off_ap = o; o = al(o + sizeof(double) * pd.n_ap);
         h.off_apq = o; o = al(o + sizeof(int32_t) * pd.n_ap);
         h.off_Om = o; o = al(o + sizeof(double) * pd.n_Om);
-        h.off_Tasc = o; o = al(o + sizeof(double) * pd.nOT);
+        h.off_Tasc = o; o = al(o + sizeof(double) * (size_t)pd.n_Om * pd.n_T);
+        h.off_kap = o; o = al(o + sizeof(double) * pd.n_kap);
+        h.off_eta = o; o = al(o + sizeof(double) * pd.n_eta);
         h.off_ps = o; o = al(o + sizeof(int64_t) * (pd.n_patch + 1));
         h.off_pos = o; o = al(o + sizeof(int32_t) * pd.S);
         h.off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)pd.S * pd.Np);
@@ -648,6 +693,8 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
         pd.ap_q = reinterpret_cast<const int32_t*>(p->ws + h.off_apq);
         pd.Om = reinterpret_cast<const double*>(p->ws + h.off_Om);
         pd.Tasc = reinterpret_cast<const double*>(p->ws + h.off_Tasc);
+        pd.kap = h.kap.empty() ? nullptr : reinterpret_cast<const double*>(p->ws + h.off_kap);
+        pd.eta = h.eta.empty() ? nullptr : reinterpret_cast<const double*>(p->ws + h.off_eta);
         pd.patch_start = reinterpret_cast<const int64_t*>(p->ws + h.off_ps);
         pd.patch_of_s = reinterpret_cast<const int32_t*>(p->ws + h.off_pos);
         pd.vn_q = reinterpret_cast<int32_t*>(p->ws + h.off_vnq);
@@ -666,6 +713,8 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
         e = e ? e : up(p->ws + h.off_apq, h.ap_q.data(), h.ap_q.size(), st);
         e = e ? e : up(p->ws + h.off_Om, h.Om.data(), h.Om.size(), st);
         e = e ? e : up(p->ws + h.off_Tasc, h.Tasc.data(), h.Tasc.size(), st);
+        if (!h.kap.empty()) e = e ? e : up(p->ws + h.off_kap, h.kap.data(), h.kap.size(), st);
+        if (!h.eta.empty()) e = e ? e : up(p->ws + h.off_eta, h.eta.data(), h.eta.size(), st);
         e = e ? e : up(p->ws + h.off_ps, h.ps.data(), h.ps.size(), st);
         e = e ? e : up(p->ws + h.off_pos, h.patch_of_s.data(), h.patch_of_s.size(), st);
         if (e) return BSH_ERR_CUDA;
@@ -946,15 +995,14 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
     if (!hp || !query || count < 0 || !row_bits || !out || !path) return BSH_ERR_ARG;
     const bsh_problem& d = *hp;
     if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || !d.v || !d.t || !d.sky || !d.a_p || !d.Omega ||
-        !d.T_asc || d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || d.n_f0 <= 0 || !finite_pos(d.v_max))
+        !d.T_asc || d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || d.n_f0 <= 0 || !finite_pos(d.v_max) ||
+        d.n_kappa < 0 || d.n_eta < 0 || (d.n_kappa > 0 && !d.kappa) || (d.n_eta > 0 && !d.eta))
         return BSH_ERR_ARG;
     bsh_plan tmp;
     tmp.threads = 256;
     ProbHost h;
     h.d = d;
-    h.ap.assign(d.a_p, d.a_p + d.n_ap);
-    h.Om.assign(d.Omega, d.Omega + d.n_Om);
-    h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
+    copy_grid(h, d);
     const int64_t ps[2] = {0, d.S};
     h.ps.assign(ps, ps + 2);
     h.d.n_patch = 1;
@@ -973,10 +1021,20 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
         volatile double t12 = t1 + t2;
         const double vn = t12 + t3;
         const int iap = b % d.n_ap, ot = b / d.n_ap;
-        const double Om = h.Om[ot / d.n_T], Ta = h.Tasc[ot];
+        const int ie = ot % pd.n_eta, ik = (ot / pd.n_eta) % pd.n_kap, r = ot / pd.n_eta / pd.n_kap;
+        const double Om = h.Om[r / d.n_T], Ta = h.Tasc[r];
+        const double kap = h.kap.empty() ? 0.0 : h.kap[ik], eta = h.eta.empty() ? 0.0 : h.eta[ie];
         volatile double dt = d.t[i] - Ta;
         volatile double arg = Om * dt;
-        const double c = Om * std::cos(arg);
+        volatile double g = std::cos(arg);
+        if (kap != 0.0 || eta != 0.0) {
+            volatile double a2 = 2.0 * arg;
+            volatile double kc = kap * std::cos(a2);
+            volatile double es = eta * std::sin(a2);
+            volatile double g1 = g + kc;
+            g = g1 + es;
+        }
+        const double c = Om * g;
         const int vq = (int)std::nearbyint(vn * sv);
         const int cq = (int)std::nearbyint(c * sc);
         const int F2a = (int)std::llround(2.0 * d.F0) + 2 * j0;
@@ -1124,9 +1182,12 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     pd.n_ap = d.n_ap;
     pd.n_Om = d.n_Om;
     pd.n_T = d.n_T;
-    pd.nOT = d.n_Om * d.n_T;
-    const long long B = (long long)d.n_ap * pd.nOT;
+    pd.n_kap = std::max(1, d.n_kappa);
+    pd.n_eta = std::max(1, d.n_eta);
+    const long long rows = orbit_rows(d);
+    const long long B = (long long)d.n_ap * rows;
     if (B > (1LL << 30) || (double)B * d.n_f0 * d.S > 9.0e18) return BSH_ERR_RANGE;
+    pd.nOT = (int)rows;
     pd.B = (int)B;
     pd.w_dtype = d.w_dtype;
     pd.F0 = d.F0;
@@ -1136,6 +1197,7 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     double ap_max = 0.0, Om_max = 0.0;
     for (int k = 0; k < d.n_ap; ++k) ap_max = std::max(ap_max, d.a_p[k]);
     for (int k = 0; k < d.n_Om; ++k) Om_max = std::max(Om_max, d.Omega[k]);
+    Om_max *= 1.0 + ecc_bound(d);
     // the same fixed-point scales as a plan of this problem
     const int nb = (d.n_f0 + JW - 1) / JW;
     const int JB = (d.n_f0 + nb - 1) / nb;
@@ -1154,7 +1216,9 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     const size_t off_ap = o; o = al(o + sizeof(double) * d.n_ap);
     const size_t off_apq = o; o = al(o + sizeof(int32_t) * d.n_ap);
     const size_t off_Om = o; o = al(o + sizeof(double) * d.n_Om);
-    const size_t off_Ta = o; o = al(o + sizeof(double) * pd.nOT);
+    const size_t off_Ta = o; o = al(o + sizeof(double) * (size_t)d.n_Om * d.n_T);
+    const size_t off_kap = o; o = al(o + sizeof(double) * pd.n_kap);
+    const size_t off_eta = o; o = al(o + sizeof(double) * pd.n_eta);
     const size_t off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)d.S * pd.Np);
     const size_t off_w = o; o = al(o + sizeof(float) * (size_t)d.S * pd.Np);
     const size_t off_cq = o; o = al(o + sizeof(int32_t) * (size_t)pd.nOT * pd.Np);
@@ -1175,6 +1239,8 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     pd.ap_q = reinterpret_cast<const int32_t*>(base + off_apq);
     pd.Om = reinterpret_cast<const double*>(base + off_Om);
     pd.Tasc = reinterpret_cast<const double*>(base + off_Ta);
+    pd.kap = d.n_kappa > 0 ? reinterpret_cast<const double*>(base + off_kap) : nullptr;
+    pd.eta = d.n_eta > 0 ? reinterpret_cast<const double*>(base + off_eta) : nullptr;
     pd.vn_q = reinterpret_cast<int32_t*>(base + off_vnq);
     pd.w32 = reinterpret_cast<float*>(base + off_w);
     pd.c_q = reinterpret_cast<int32_t*>(base + off_cq);
@@ -1182,7 +1248,12 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     cudaError_t e = cudaMemcpyAsync(base + off_pd, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
     e = e ? e : cudaMemcpyAsync(base + off_ap, d.a_p, sizeof(double) * d.n_ap, cudaMemcpyHostToDevice, st);
     e = e ? e : cudaMemcpyAsync(base + off_Om, d.Omega, sizeof(double) * d.n_Om, cudaMemcpyHostToDevice, st);
-    e = e ? e : cudaMemcpyAsync(base + off_Ta, d.T_asc, sizeof(double) * pd.nOT, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(base + off_Ta, d.T_asc, sizeof(double) * (size_t)d.n_Om * d.n_T,
+                                cudaMemcpyHostToDevice, st);
+    if (d.n_kappa > 0)
+        e = e ? e : cudaMemcpyAsync(base + off_kap, d.kappa, sizeof(double) * d.n_kappa, cudaMemcpyHostToDevice, st);
+    if (d.n_eta > 0)
+        e = e ? e : cudaMemcpyAsync(base + off_eta, d.eta, sizeof(double) * d.n_eta, cudaMemcpyHostToDevice, st);
     if (e) return BSH_ERR_CUDA;
     const ProbDev* dpd = reinterpret_cast<const ProbDev*>(base + off_pd);
     static_ap_q<<<1, 256, 0, st>>>(dpd);

@@ -1,7 +1,10 @@
 // Track tables (Eq. (15)): the FP64 pieces of the Doppler / binary track that
 // do not depend on f0, evaluated once per call.
 //   vn_q[s][i]  = round(vn * 2^s_vn),  vn = (v_x n_x + v_y n_y) + v_z n_z
-//   c64[ot][i]  = Omega cos(Omega (t_i - t_asc)),  c_q = round(c64 * 2^s_c)
+//   c64[ot][i]  = Omega g,  g = (cos(phi) + kappa cos(2 phi)) + eta sin(2 phi),
+//                 phi = Omega (t_i - t_asc)  (Eq. (14); g = cos(phi) when kappa = eta = 0)
+//   c_q = round(c64 * 2^s_c)
+// Orbit row ot = ((iOm * n_T + iT) * n_kap + ik) * n_eta + ie.
 //   w32 / w64   = the problem's weights widened exactly (fp16/bf16/fp32 -> fp32, any -> fp64)
 // The products are rounded individually (no fused multiply-add) so that the
 // FP64 values equal those of a plain sequential evaluation of the formula.
@@ -60,10 +63,21 @@ __global__ void binary_tables(const ProbDev* __restrict__ probs, int q, unsigned
         double c = 0.0;
         int32_t cq = 0;
         if (i < P.N) {
-            const double Om = P.Om[ot / P.n_T];
-            const double Ta = P.Tasc[ot];
+            const int ie = ot % P.n_eta;
+            const int r1 = ot / P.n_eta;
+            const int ik = r1 % P.n_kap;
+            const int r = r1 / P.n_kap;          // iOm * n_T + iT
+            const double Om = P.Om[r / P.n_T];
+            const double Ta = P.Tasc[r];
+            const double kap = P.kap ? P.kap[ik] : 0.0;
+            const double eta = P.eta ? P.eta[ie] : 0.0;
             const double arg = __dmul_rn(Om, __dsub_rn(P.t[i], Ta));
-            c = __dmul_rn(Om, cos(arg));
+            double g = cos(arg);
+            if (kap != 0.0 || eta != 0.0) {
+                const double a2 = __dmul_rn(2.0, arg);
+                g = __dadd_rn(__dadd_rn(g, __dmul_rn(kap, cos(a2))), __dmul_rn(eta, sin(a2)));
+            }
+            c = __dmul_rn(Om, g);
             const double x = __dmul_rn(c, scale);
             if (!(fabs(x) < lim)) set_status(status, ST_RANGE);
             else cq = __double2int_rn(x);

@@ -307,12 +307,15 @@ def mid(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,
 
 
 def eccentric(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 16, n_P: int = 16, n_T: int = 16,
-              n_kap: int = 3, n_eta: int = 3, e_max: float = 0.02, seed: int = SEED_NOISE,
-              patch_size: int = 50, top_k: int = 1000) -> Problem:
+              n_kap: int = 3, n_eta: int = 3, e_max: float = 0.1, seed: int = SEED_NOISE,
+              patch_size: int = 50, top_k: int = 1000, sky: Optional[np.ndarray] = None) -> Problem:
     """Low-eccentricity search (Eq. (14)): the mid construction (2 x 2000 SFTs over 1 yr,
     200 Hz, patches of 50) with a 16^3 circular grid widened by kappa, eta in
-    [-e_max, e_max] (3 x 3), so B = 16^3 * 9 = 36864 binary templates."""
-    sky = fibonacci_sky(n_sky)
+    [-e_max, e_max] (3 x 3), so B = 16^3 * 9 = 36864 binary templates.  e up to
+    0.14 passes the circular model's limit 1/(2 T_c f0 a_p Omega) (0.057 at
+    a_p = 10 ls, P = 15 d) while e^2 T_c f0 a_p Omega stays below one bin."""
+    if sky is None:
+        sky = fibonacci_sky(n_sky)
     return make_problem("eccentric", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=900.0, span=YEAR_SID,
                         random_times=True, f_lo=200.0, n_f0=90, half_bin=False, sky=sky,
                         patch_size=patch_size, a_p=np.linspace(0.5, 10.0, n_ap),

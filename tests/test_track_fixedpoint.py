@@ -4,7 +4,7 @@ bsh_debug_track_windows evaluates, on the host, the exact functions the
 count kernel uses to turn a (sky point, binary template, SFT, f0 block) into
 a 32-bit peak window: fixed-point tables, the fast single-cell test, the
 crossing path and the exact FP64 fallback.  Every window bit must equal the
-peakgram bit at the oracle's track bin (Eq. (15)) of that f0 template,
+peakgram bit at the oracle's track bin (Eq. (14)/(15)) of that f0 template,
 except where the oracle flags a tie.
 """
 import numpy as np
@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1904_04873_gb300 import bsh, synth
-from _common import template_of
+from _common import orbit_of
 
 pytest.importorskip("ctypes")
 
@@ -38,11 +38,11 @@ def _check(pr, n_q, seed, force=None):
         JB = -(-pr.n_f0 // nb)
         j0 = int(rng.integers(nb)) * JB
         row = rng.integers(0, 2 ** 32, size=pr.W, dtype=np.uint64).astype(np.uint32)
-        ap, Om, Ta = template_of(pr, b)
+        ap, Om, Ta, kap, eta = orbit_of(pr, b)
         bits = np.zeros(32, np.uint32)
         tie = np.zeros(32, bool)
         for j in range(32):
-            k, t = oracle.track_bin(pr.F0 + j0 + j, pr.v[i], pr.sky[s], ap, Om, Ta, pr.t[i])
+            k, t = oracle.track_bin_ell1(pr.F0 + j0 + j, pr.v[i], pr.sky[s], ap, Om, Ta, kap, eta, pr.t[i])
             col = k - pr.k_lo
             assert 0 <= col < 32 * pr.W
             bits[j] = (row[col >> 5] >> np.uint32(col & 31)) & 1
@@ -90,3 +90,10 @@ def test_forced_exact_ties_use_fp64_fallback():
 def test_half_bin_grid_windows():
     pr = synth.precision_stress(n_sky=64, n_per_det=300, n_ap=8, n_P=8, n_T=8)
     _check(pr, 3000, 5)
+
+
+def test_eccentric_grid_windows():
+    # kappa, eta in [-0.05, 0.05]: the fixed-point scales widen to Omega (1 + |kappa| + |eta|)
+    pr = synth.eccentric(n_sky=64, n_per_det=300, n_ap=6, n_P=4, n_T=4, n_kap=3, n_eta=3, e_max=0.05)
+    path, _ = _check(pr, 4000, 6)
+    assert (path == 0).mean() > 0.9

@@ -63,6 +63,16 @@ def test_static_power_sum_matches_plan_twice():
     _check(dp1, ref1)
 
 
+def test_static_power_sum_eccentric_grid():
+    # the ELL1 orbit rows (kappa, eta of Eq. (14)) are expanded in the static tables too
+    from paper_1904_04873_gb300 import synth
+    pr = synth.eccentric(n_sky=6, n_per_det=150, n_ap=4, n_P=2, n_T=2, n_kap=3, n_eta=2, e_max=0.05,
+                         patch_size=3, top_k=25)
+    dp, _, _ = device_problem(pr, "f16")
+    ref = _reference(dp, 25)
+    _check(dp, ref)
+
+
 def test_static_power_sum_rejects_oversized_problem():
     pr = small_mid(n_sky=2, n_per_det=64, n_ap=2, n_P=2, n_T=2, patch_size=2, top_k=5)
     dp, _, _ = device_problem(pr, "f16")
