@@ -60,6 +60,7 @@ class Problem(ctypes.Structure):
         ("Om", ctypes.c_void_p), ("n_T", ctypes.c_int), ("Tasc", ctypes.c_void_p),
         ("rho_th", ctypes.c_double), ("tie_band", ctypes.c_double),
         ("n_kap", ctypes.c_int), ("kap", ctypes.c_void_p), ("n_eta", ctypes.c_int), ("eta", ctypes.c_void_p),
+        ("lut_block", ctypes.c_int),
     ]
 
 
@@ -201,7 +202,7 @@ class OracleProblem:
     """Holds contiguous arrays alive for the ctypes struct."""
 
     def __init__(self, *, bits, w, v, t, F0, n_f0, sky, a_p, Omega, T_asc, k_lo, K, rho=None,
-                 rho_th: float = 1.6, tie_band: float = TIE_BAND, kappa=None, eta=None):
+                 rho_th: float = 1.6, tie_band: float = TIE_BAND, kappa=None, eta=None, lut_block: int = 0):
         self.bits = _c(bits, np.uint32)
         self.w = _c(w, np.float64)
         self.v = _c(v, np.float64)
@@ -231,7 +232,8 @@ class OracleProblem:
                          n_kap=0 if self.kap is None else self.kap.size,
                          kap=None if self.kap is None else self.kap.ctypes.data,
                          n_eta=0 if self.eta is None else self.eta.size,
-                         eta=None if self.eta is None else self.eta.ctypes.data)
+                         eta=None if self.eta is None else self.eta.ctypes.data,
+                         lut_block=int(lut_block))
 
     def count_one(self, s: int, b: int, j: int):
         nu, nw, nt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()

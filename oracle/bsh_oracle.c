@@ -270,7 +270,24 @@ typedef struct {
     const double* kap;    /* [n_kap] e cos(omega), or NULL with n_kap = 0 */
     int n_eta;
     const double* eta;    /* [n_eta] e sin(omega), or NULL with n_eta = 0 */
+    int lut_block;        /* 0: exact track; L > 0: look-up-table approximation, blocks of L f0 */
 } orc_problem;
+
+/* Look-up-table approximation of stage 1 (Sec. IV.B): the modulation F D of  */
+/* the track is evaluated once per block of L contiguous f0 templates, at the */
+/* block's reference template, and reused for the other templates of the      */
+/* block, whose bins are the reference bins shifted by their f0 offset:       */
+/*   k_j = floor(F_ref + F_ref D + 1/2) + (j - j_ref).                        */
+/* Block q holds j in [qL, min(qL + L, n_f0)); its reference is its middle    */
+/* template j_ref = qL + (len - 1)/2 (len = the block's length, integer       */
+/* division).  L = 1 is the exact track.                                      */
+static int lut_ref(const orc_problem* pr, int j) {
+    int L = pr->lut_block;
+    int q = j / L;
+    int len = pr->n_f0 - q * L;
+    if (len > L) len = L;
+    return q * L + (len - 1) / 2;
+}
 
 static void template_params(const orc_problem* pr, int64_t b, double* ap, double* Om, double* Ta,
                             double* kap, double* eta) {
@@ -300,6 +317,13 @@ int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
                   int32_t* unw_lo, int32_t* unw_hi, double* w_lo, double* w_hi) {
     double ap, Om, Ta, kap, eta;
     template_params(pr, b, &ap, &Om, &Ta, &kap, &eta);
+    /* the track is evaluated at F (exact) or at the block's reference F_ref (LUT) */
+    int shift = 0;
+    if (pr->lut_block > 0) {
+        int jr = lut_ref(pr, j);
+        shift = j - jr;
+        j = jr;
+    }
     double F = pr->F0 + (double)j;
     const double* n = pr->sky + 3 * (size_t)s;
     int32_t cu = 0, ties = 0, lo = 0, hi = 0;
@@ -307,7 +331,7 @@ int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
     for (int i = 0; i < pr->N; ++i) {
         int tie;
         int64_t k = orc_track_bin_ell1(F, pr->v + 3 * (size_t)i, n, ap, Om, Ta, kap, eta, pr->t[i],
-                                       pr->tie_band, &tie);
+                                       pr->tie_band, &tie) + shift;
         int64_t col = k - pr->k_lo;
         if (col < 0 || col >= pr->K) return ORC_ERR_RANGE;
         const uint32_t* row = pr->bits + (size_t)i * pr->W;
