@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
+    ap.add_argument("--track", choices=["exact", "lut"], default="exact",
+                    help="exact track (default) or the look-up-table approximation of Sec. IV.B")
     return ap.parse_args()
 
 
@@ -296,7 +298,8 @@ def main():
     pr = make_problem(args.workload, rank)
     stream = torch.cuda.current_stream()
     dp = bsh.DeviceProblem(pr, w_dtype="f16")
-    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=args.threads, sft_chunk=args.chunk)
+    mode = bsh.MODE_LUT if args.track == "lut" else bsh.MODE_BATCHED
+    plan = bsh.Plan([dp], mode, top_k=pr.top_k, threads=args.threads, sft_chunk=args.chunk)
     n_cf = 100
     dp.prepare()
     tile = plan.tile() if args.no_tune else plan.autotune()
@@ -445,7 +448,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
                 "config": workload_config(pr, args.workload) | {"parallelism": f"replicas x{world}",
-                                                                  "graph": bool(args.graph), "tile": tile},
+                                                                  "graph": bool(args.graph), "tile": tile,
+                                                                  "track": args.track},
                 "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
                 "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline,
                 "plain": plain, "cpu_baseline": cpu}

@@ -66,7 +66,14 @@ enum { BSH_F64 = 0, BSH_F32 = 1, BSH_F16 = 2, BSH_BF16 = 3 };
 enum {
     BSH_MODE_BATCHED = 0,   /* one persistent launch over every problem and patch, fixed-point
                                track with exact FP64 fallback, FP32 Kahan-compensated sums */
-    BSH_MODE_PLAIN = 1      /* one launch per sky patch, FP64 track for every term, FP64 sums */
+    BSH_MODE_PLAIN = 1,     /* one launch per sky patch, FP64 track for every term, FP64 sums */
+    BSH_MODE_LUT = 2        /* BATCHED with the look-up-table approximation of Sec. IV.B in the
+                               number count: in each f0 block of L = ceil(n_f0 / ceil(n_f0 / 32))
+                               templates (block q: j in [qL, min(qL + L, n_f0)), length len), the
+                               modulation F D is evaluated at the middle template
+                               j_ref = qL + (len - 1)/2 only and reused:
+                               k_j = floor(F_ref + F_ref D + 1/2) + (j - j_ref).  Stage 2
+                               (bsh_power_sum) keeps the exact track. */
 };
 
 /* Text for a status code (static storage). */

@@ -21,7 +21,7 @@ _lib = None
 
 OK, ERR_ARG, ERR_RANGE, ERR_TIMEOUT, ERR_CUDA, ERR_WORKSPACE, ERR_STATE = range(7)
 F64, F32, F16, BF16 = range(4)
-MODE_BATCHED, MODE_PLAIN = 0, 1
+MODE_BATCHED, MODE_PLAIN, MODE_LUT = 0, 1, 2
 DTYPE_CODES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 
 

@@ -12,8 +12,12 @@
 //   Z(j)   = round(F_j * vn * 2^s_y) + (frac(F_j) + 1/2) 2^s_y    from vn_q = round(vn 2^s_vn)
 //   C_q(j) = round(F_j * c * 2^s_C)                               from c_q  = round(c 2^s_c), c = Omega g
 //   ap_q   = round(a_p 2^s_a),  s_y = s_a + s_C - 32
-// and the bin is floor(F_j) + floor(v(j) / 2^s_y).  Since v is linear in j, a
-// block of 32 consecutive f0 templates needs v only at j0 and j0 + 31.
+// and the bin is floor(F_j) + floor(v(j) / 2^s_y).  The exact value is linear in
+// j with slope D 2^s_y, so a block of 32 consecutive f0 templates [j0, j0 + 31]
+// reads one 32-bit window when v at the reference template j0 + 15, widened by
+// the margin mg = 16 |D|max 2^s_y + M, stays inside one cell; |D|max is bounded
+// per SFT from vn_q and the problem's a_p Omega bound (fp_margin).  Otherwise v
+// is evaluated at both ends of the block (fp_window_slow).
 #pragma once
 
 #include <cstdint>
@@ -54,6 +58,8 @@ struct FixedPoint {
     int M;                        // decision margin (units of 2^-s_y bins)
     int off_q;                    // (frac(F0) + 1/2) 2^s_y
     double eps;                   // error bound of v (units of 2^-s_y bins)
+    int mg_a;                     // 16 a_p,max |c|max 2^s_y + M + 2: binary part of the slope margin
+    int mg_k;                     // (|vn_q| + 2^mg_k) >> mg_k >= 16 |vn| 2^s_y (vn part of the margin)
 };
 
 // Per-problem data seen by the kernels.
@@ -159,6 +165,17 @@ __host__ __device__ __forceinline__ int make_C(int F2, int c_q, const FixedPoint
     return (int)r;
 }
 
+// Margin of the reference-template test for an SFT with table entry vn_q.
+__host__ __device__ __forceinline__ int fp_margin(int vn_q, const FixedPoint& fp) {
+    const unsigned a = (unsigned)(vn_q < 0 ? -vn_q : vn_q);
+    return fp.mg_a + (int)((a + (1u << fp.mg_k)) >> fp.mg_k);
+}
+
+// Reference-template test: v widened by mg on both sides stays in one cell.
+__host__ __device__ __forceinline__ bool fp_fast_ref(int v, int mg, int s_y) {
+    return ((unsigned)((v - mg) ^ (v + mg)) >> s_y) == 0u;
+}
+
 // Fast path: both ends of the block, widened by M, fall in the same bin cell.
 __host__ __device__ __forceinline__ bool fp_fast(int v0, int v1, int s_y, int M) {
     int lo = imin(v0, v1) - M;
@@ -181,51 +198,68 @@ __host__ __device__ __forceinline__ uint32_t row_bit(const uint32_t* row, int po
     return (row[pos >> 5] >> (pos & 31)) & 1u;
 }
 
-// Slow path of the window: the block's ends are near a rounding boundary or
-// on both sides of one.  V_j = 31 v0 + d j (d = v1 - v0) is 31 v(j) exactly
-// interpolated; the cell of each j is decided from V_j when it is at least
-// 31 M from a boundary, else by the exact FP64 expression (exact_o(j) returns
-// floor(F_j + F_j D + 1/2) - floor(F_j)).  path: 1 = single clean crossing,
-// 2 = per-template decision.  Bits whose position falls outside the staged
-// row set *bad and read as 0.
+// Two-ended test of a block whose reference-template test failed.  V_j = 31 v0 + d j
+// (d = v1 - v0) is 31 v(j) exactly interpolated.  Path 0: both ends, widened by M,
+// in one cell.  Path 1: the ends in adjacent cells and a single crossing at least
+// 31 M from every template point: templates below the crossing read the first cell,
+// the others the second.  Returns false (path 2) when neither holds; the caller then
+// decides template by template (fp_window_exact).
+__host__ __device__ __forceinline__ bool fp_window_ends(int v0, int v1, int pbase, int pos_max, int s, int M,
+                                                        const uint32_t* row, uint32_t* out, int* path) {
+    const int vmin = imin(v0, v1), vmax = imax(v0, v1);
+    const int ca = vmin >> s, cb = vmax >> s;
+    if (((unsigned)((vmin - M) ^ (vmax + M)) >> s) == 0u) {
+        const int p0 = pbase + ca;
+        if ((unsigned)p0 > (unsigned)pos_max) return false;
+        *path = 0;
+        *out = row_window(row, p0);
+        return true;
+    }
+    if (cb != ca + 1) return false;
+    const long long lo_edge = (long long)ca << s, Bc = (long long)cb << s, hi_edge = ((long long)cb + 1) << s;
+    if ((long long)vmin - lo_edge < M || hi_edge - (long long)vmax < M) return false;
+    const long long d = (long long)v1 - (long long)v0;       // nonzero: the ends are in different cells
+    const long long B31 = 31LL * Bc, V0 = 31LL * v0;
+    // jc = first j with V_j on the far side of 31 Bc; estimated in single precision
+    // (error below one step) and settled with exact integer comparisons
+    const float est = (float)(B31 - V0) / (float)d;
+    int jc = (int)ceilf(est);
+    jc = jc < 0 ? 0 : (jc > 32 ? 32 : jc);
+    for (int it = 0; it < 2; ++it) {
+        const bool far_jc = d > 0 ? (V0 + d * jc >= B31) : (V0 + d * jc < B31);
+        const bool far_prev = jc > 0 && (d > 0 ? (V0 + d * (jc - 1) >= B31) : (V0 + d * (jc - 1) < B31));
+        if (far_prev) --jc;
+        else if (!far_jc && jc < 32) ++jc;
+        else break;
+    }
+    if (jc < 1 || jc > 31) return false;
+    const long long Vm = V0 + d * (jc - 1), Vp = V0 + d * jc;
+    const bool ok_m = d > 0 ? (Vm < B31) : (Vm >= B31);
+    const bool ok_p = d > 0 ? (Vp >= B31) : (Vp < B31);
+    const long long M31 = 31LL * M;
+    const long long dm = Vm > B31 ? Vm - B31 : B31 - Vm;
+    const long long dp = Vp > B31 ? Vp - B31 : B31 - Vp;
+    if (!ok_m || !ok_p || dm < M31 || dp < M31) return false;
+    const int o0 = v0 >> s;
+    const int o1 = d > 0 ? o0 + 1 : o0 - 1;
+    const int p0 = pbase + o0, p1 = pbase + o1;
+    if ((unsigned)p0 > (unsigned)pos_max || (unsigned)p1 > (unsigned)pos_max) return false;
+    const uint32_t low = (1u << jc) - 1u;
+    *path = 1;
+    *out = (row_window(row, p0) & low) | (row_window(row, p1) & ~low);
+    return true;
+}
+
+// Path 2: each template's cell from V_j when it is at least 31 M from a boundary, else
+// by the exact FP64 expression (exact_o(j) returns floor(F_j + F_j D + 1/2) - floor(F_j)).
+// Bits whose position falls outside the staged row set *bad and read as 0.
 template <class ExactO>
-__host__ __device__ uint32_t fp_window_slow(int v0, int v1, int pbase, int pos_max, int s,
-                                            int M, const uint32_t* row, ExactO exact_o,
-                                            int* path, bool* bad) {
+__host__ __device__ uint32_t fp_window_exact(int v0, int v1, int pbase, int pos_max, int s, int M,
+                                             const uint32_t* row, ExactO exact_o, bool* bad) {
     const long long d = (long long)v1 - (long long)v0;
     const long long S31 = 31LL << s;
     const long long M31 = 31LL * M;
-    const int vmin = imin(v0, v1), vmax = imax(v0, v1);
-    const int ca = vmin >> s, cb = vmax >> s;
-    if (cb == ca + 1) {
-        const long long lo_edge = (long long)ca << s;
-        const long long Bc = (long long)cb << s;
-        const long long hi_edge = ((long long)cb + 1) << s;
-        if ((long long)vmin - lo_edge >= M && hi_edge - (long long)vmax >= M) {
-            const long long num = 31LL * (Bc - (long long)v0);
-            int jc;
-            if (d > 0) jc = (int)((num + d - 1) / d);        // first j with V_j >= 31 Bc
-            else jc = (int)((-num) / (-d)) + 1;               // first j with V_j < 31 Bc
-            if (jc >= 1 && jc <= 31) {
-                const long long B31 = 31LL * Bc;
-                const long long Vm = 31LL * v0 + d * (jc - 1);
-                const long long Vp = 31LL * v0 + d * jc;
-                const long long dm = Vm > B31 ? Vm - B31 : B31 - Vm;
-                const long long dp = Vp > B31 ? Vp - B31 : B31 - Vp;
-                if (dm >= M31 && dp >= M31) {
-                    const int o0 = v0 >> s;
-                    const int o1 = d > 0 ? o0 + 1 : o0 - 1;
-                    const int p0 = pbase + o0, p1 = pbase + o1;
-                    if ((unsigned)p0 <= (unsigned)pos_max && (unsigned)p1 <= (unsigned)pos_max) {
-                        const uint32_t low = (1u << jc) - 1u;
-                        *path = 1;
-                        return (row_window(row, p0) & low) | (row_window(row, p1) & ~low);
-                    }
-                }
-            }
-        }
-    }
-    *path = 2;
+    const int ca = imin(v0, v1) >> s;
     uint32_t m = 0;
     const long long base = 31LL * ((long long)ca << s);
     for (int j = 0; j < 32; ++j) {
@@ -241,6 +275,17 @@ __host__ __device__ uint32_t fp_window_slow(int v0, int v1, int pbase, int pos_m
         m |= row_bit(row, pos) << j;
     }
     return m;
+}
+
+// Both together (host checks and the plain tools): path 0, 1 or 2.
+template <class ExactO>
+__host__ __device__ uint32_t fp_window_slow(int v0, int v1, int pbase, int pos_max, int s,
+                                            int M, const uint32_t* row, ExactO exact_o,
+                                            int* path, bool* bad) {
+    uint32_t m = 0;
+    if (fp_window_ends(v0, v1, pbase, pos_max, s, M, row, &m, path)) return m;
+    *path = 2;
+    return fp_window_exact(v0, v1, pbase, pos_max, s, M, row, exact_o, bad);
 }
 
 
@@ -275,6 +320,7 @@ struct CountArgs {
     int max_n;                   // largest SFT count of the problems
     int wrows;                   // Omega-T rows one warp needs at most
     int acc_mode;                // weighted accumulation variant of the batched kernel
+    int lut;                     // 1: look-up-table approximation of the track (BSH_MODE_LUT)
 };
 
 struct TmapSet {

@@ -99,7 +99,7 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 // per-thread Kahan sums, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, cp, acc, comp, tab, bar, done, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, ye, cp, ce, acc, comp, tab, bar, done, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
@@ -113,7 +113,9 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     for (int b = 0; b < 2; ++b) { L.w[b] = o; o = align128(o + I * 4); }
     for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + I * ot_max * 4); }
     L.y = o; o = align128(o + nw * I * 8);
-    L.cp = o; o = align128(o + nw * I * wrows * 8);
+    L.ye = o; o = align128(o + nw * I * 8);
+    L.cp = o; o = align128(o + nw * I * wrows * 4);
+    L.ce = o; o = align128(o + nw * I * wrows * 8);
     L.acc = o; o = align128(o + JW * threads * 4);
     L.comp = o; o = align128(o + JW * threads * 4);
     L.tab = o; o = align128(o + (acc ? nw * 256 * 4 : 0));
@@ -135,7 +137,7 @@ struct TopSmem {
 
 // Per-item constants shared by every thread.
 struct ItemCtx {
-    int q, s, fb, bt, j0, jb, c0, pbase, ot0, nrows, F2a, region, nchunks;
+    int q, s, fb, bt, j0, jb, c0, pbase, ot0, nrows, F2a, F2r, region, nchunks;
     uint32_t lid_base;
 };
 
@@ -158,6 +160,7 @@ __device__ __forceinline__ ItemCtx item_ctx(const CountArgs& a, const Item& it, 
     c.ot0 = b0 / P.n_ap;
     c.nrows = b1 / P.n_ap - c.ot0 + 1;
     c.F2a = (int)llrint(2.0 * P.F0) + 2 * c.j0;
+    c.F2r = c.F2a + 2 * ((c.jb - 1) / 2);   // 2 F of the block's middle template (LUT reference)
     const int patch = P.patch_of_s[it.s];
     c.region = P.region_base + patch;
     c.lid_base = (uint32_t)((long long)(it.s - (int)P.patch_start[patch]) * P.B);
@@ -201,10 +204,11 @@ __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32
     l = u ^ c;
 }
 
-// Exact FP64 fallback for one template block at one SFT (rare).
-__device__ __noinline__ uint32_t slow_window(const ProbDev& P, int v0, int v1, int pbase, int pos_max,
-                                             const uint32_t* row, int s, int b, int i, int j0,
-                                             unsigned* status) {
+// Template-by-template decision of one block at one SFT (rare): the ends are near a
+// rounding boundary; FP64 decides the templates within 31 M of it.
+__device__ __forceinline__ uint32_t slow_window_exact(const ProbDev& P, int v0, int v1, int pbase, int pos_max,
+                                                   const uint32_t* row, int s, int b, int i, int j0,
+                                                   unsigned* status) {
     bool have = false;
     double D = 0.0;
     auto exact_o = [&](int j) -> int {
@@ -224,11 +228,30 @@ __device__ __noinline__ uint32_t slow_window(const ProbDev& P, int v0, int v1, i
         const double k = floor(__dadd_rn(x, 0.5));
         return (int)((long long)k - (long long)(P.G0 + j0 + j));
     };
-    int path = 0;
     bool bad = false;
-    const uint32_t m = fp_window_slow(v0, v1, pbase, pos_max, P.fp.s_y, P.fp.M, row, exact_o, &path, &bad);
+    const uint32_t m = fp_window_exact(v0, v1, pbase, pos_max, P.fp.s_y, P.fp.M, row, exact_o, &bad);
     if (bad) set_status(status, ST_RANGE);
     return m;
+}
+
+// Exact FP64 fallback of the look-up-table variant: the modulation at the block's
+// reference template jr, near a rounding boundary (rare).
+__device__ __noinline__ uint32_t slow_window_lut(const ProbDev& P, int pbase, int pos_max, const uint32_t* row,
+                                                 int s, int b, int i, int jr, unsigned* status) {
+    const double* n = P.sky + 3 * (size_t)s;
+    const double* v = P.v + 3 * (size_t)i;
+    const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])), __dmul_rn(v[2], n[2]));
+    const double c = P.c64[(size_t)(b / P.n_ap) * P.Np + i];
+    const double D = __dsub_rn(vn, __dmul_rn(P.a_p[b % P.n_ap], c));
+    const double F = P.F0 + (double)jr;
+    const double x = __dadd_rn(F, __dmul_rn(F, D));
+    const int o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)(P.G0 + jr));
+    const int pos = pbase + o;
+    if (pos < 0 || pos > pos_max) {
+        set_status(status, ST_RANGE);
+        return 0u;
+    }
+    return row_window(row, pos);
 }
 
 // ------------------------------------------------------------ toplist pieces
@@ -348,7 +371,9 @@ __device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, 
 // 1 = per 8 SFTs, a warp-private table of the 256 subset sums of their weights
 // and one lookup per f0 template (the 8 window masks are bit-transposed so
 // that byte j holds template j's 8 bits).
-template <int THREADS, int NE, int ACC>
+// LUT = true: the look-up-table approximation of Sec. IV.B -- every template of an f0
+// block reads the window at the block's reference template's modulation.
+template <int THREADS, int NE, int ACC, bool LUT>
 __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -363,8 +388,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int I = a.chunk;
     const int wrows = a.wrows;
-    int2* yp = reinterpret_cast<int2*>(smem + L.y) + warp * I;
-    int2* cp = reinterpret_cast<int2*>(smem + L.cp) + warp * I * wrows;
+    int2* yp = reinterpret_cast<int2*>(smem + L.y) + warp * I;       // Z at the reference, margin
+    int2* ype = reinterpret_cast<int2*>(smem + L.ye) + warp * I;     // Z at j0, j0 + 31
+    int* cp = reinterpret_cast<int*>(smem + L.cp) + warp * I * wrows;            // C at the reference
+    int2* cpe = reinterpret_cast<int2*>(smem + L.ce) + warp * I * wrows;         // C at j0, j0 + 31
     float* tab = reinterpret_cast<float*>(smem + L.tab) + warp * 256;
 
     long long it = a.cta_item[blockIdx.x];
@@ -437,7 +464,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
 #pragma unroll
         for (int k = 0; k < NE; ++k) e8[k] = 0;
 
-        const int F2a = cur.F2a, F2b = cur.F2a + 62;
+        // track values at the reference template (the block's j0 + 15; the LUT's middle template)
+        const int F2a = cur.F2a, F2b = cur.F2a + 62, F2ref = LUT ? cur.F2r : cur.F2a + 30;
         const FixedPoint fpl = P.fp;
         bool aborted = false;
         for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
@@ -450,17 +478,21 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 aborted = true;
                 break;
             }
-            // this warp's track pairs for the chunk: Z and C_q at j0 and j0 + 31
+            // this warp's track values for the chunk: Z at the reference template with the SFT's
+            // margin (the slope bound; M alone for the LUT), C_q at the reference template, and
+            // both at the block's ends for the two-ended test
             const int32_t* vnr = reinterpret_cast<const int32_t*>(smem + L.vn[buf]);
             const int32_t* cr = reinterpret_cast<const int32_t*>(smem + L.c[buf]);
             for (int e = lane; e < I; e += 32) {
                 const int vq = vnr[e];
-                yp[e] = make_int2(make_Z(F2a, vq, fpl), make_Z(F2b, vq, fpl));
+                yp[e] = make_int2(make_Z(F2ref, vq, fpl), LUT ? fpl.M : fp_margin(vq, fpl));
+                if (!LUT) ype[e] = make_int2(make_Z(F2a, vq, fpl), make_Z(F2b, vq, fpl));
             }
             for (int e = lane; e < I * nrw; e += 32) {
                 const int r = e / I, il = e - r * I;
                 const int cq = cr[(orow0 + r) * I + il];
-                cp[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
+                cp[il * wrows + r] = make_C(F2ref, cq, fpl);
+                if (!LUT) cpe[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
             }
             __syncwarp();
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
@@ -473,28 +505,37 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 for (int u = 0; u < 8; ++u) {
                     const int il = g8 + u;
                     const int2 z = yp[il];
-                    const int2 cc = cp[il * wrows + ot];
-                    const int v0 = z.x - __mulhi(apq, cc.x);
-                    const int v1 = z.y - __mulhi(apq, cc.y);
+                    const int v = z.x - __mulhi(apq, cp[il * wrows + ot]);
                     // in the staged segment by construction (host band check, device velocity
                     // check); the clamp only keeps the read in bounds
-                    const unsigned pos = min((unsigned)(pbase + (v0 >> s_y)), (unsigned)pos_max);
+                    const unsigned pos = min((unsigned)(pbase + (v >> s_y)), (unsigned)pos_max);
                     mk[u] = row_window(pk + il * wseg, (int)pos);
-                    slow |= (fp_fast(v0, v1, s_y, M) ? 0u : 1u) << u;
+                    slow |= (fp_fast_ref(v, z.y, s_y) ? 0u : 1u) << u;
                 }
-                if (slow) {       // rare: boundary crossing or near-boundary terms
-#pragma unroll 1
-                    for (int u = 0; u < 8; ++u) {
-                        if (!((slow >> u) & 1u)) continue;
+                if (slow) {       // rare: near a rounding boundary; each lane takes its next entry
+                    unsigned sl = slow;
+                    while (sl) {
+                        const int u = __ffs(sl) - 1;
+                        sl &= sl - 1u;
                         const int il = g8 + u;
-                        const int2 z = yp[il];
-                        const int2 cc = cp[il * wrows + ot];
-                        const int v0 = z.x - __mulhi(apq, cc.x);
-                        const int v1 = z.y - __mulhi(apq, cc.y);
-                        mk[u] = (bvalid && i0 + il < P.N)
-                                    ? slow_window(P, v0, v1, pbase, pos_max, pk + il * wseg, cur.s, b, i0 + il,
-                                                  cur.j0, a.status)
-                                    : 0u;
+                        uint32_t wv = 0u;
+                        if (bvalid && i0 + il < P.N) {
+                            if (LUT) {
+                                wv = slow_window_lut(P, pbase, pos_max, pk + il * wseg, cur.s, b, i0 + il,
+                                                     cur.j0 + (cur.jb - 1) / 2, a.status);
+                            } else {
+                                const int2 ze = ype[il];
+                                const int2 ce = cpe[il * wrows + ot];
+                                const int v0 = ze.x - __mulhi(apq, ce.x);
+                                const int v1 = ze.y - __mulhi(apq, ce.y);
+                                int path;
+                                if (!fp_window_ends(v0, v1, pbase, pos_max, s_y, M, pk + il * wseg, &wv, &path))
+                                    wv = slow_window_exact(P, v0, v1, pbase, pos_max, pk + il * wseg, cur.s, b,
+                                                           i0 + il, cur.j0, a.status);
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) mk[k] = (k == u) ? wv : mk[k];
                     }
                 }
                 if (ACC == 0) {
@@ -692,25 +733,29 @@ void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads
         return;
     }
     const bool small_n = a.max_n < 8 * 1024;
-#define BSH_LAUNCH_BATCHED(T, NE, ACC)                                            \
+#define BSH_LAUNCH_BATCHED(T, NE, ACC, LUT)                                       \
     do {                                                                          \
         static int s_done = 0;                                                    \
-        ensure_smem(count_batched<T, NE, ACC>, a.smem_bytes, &s_done);            \
-        count_batched<T, NE, ACC><<<grid, T, a.smem_bytes, st>>>(a, maps);        \
+        ensure_smem(count_batched<T, NE, ACC, LUT>, a.smem_bytes, &s_done);       \
+        count_batched<T, NE, ACC, LUT><<<grid, T, a.smem_bytes, st>>>(a, maps);   \
+    } while (0)
+#define BSH_LAUNCH_ACC(T, NE, LUT)                                                \
+    do {                                                                          \
+        if (a.acc_mode) BSH_LAUNCH_BATCHED(T, NE, 1, LUT);                        \
+        else BSH_LAUNCH_BATCHED(T, NE, 0, LUT);                                   \
+    } while (0)
+#define BSH_LAUNCH_NE(T, LUT)                                                     \
+    do {                                                                          \
+        if (small_n) BSH_LAUNCH_ACC(T, 10, LUT);                                  \
+        else BSH_LAUNCH_ACC(T, 13, LUT);                                          \
     } while (0)
     if (threads == 128) {
-        if (small_n) {
-            if (a.acc_mode) BSH_LAUNCH_BATCHED(128, 10, 1); else BSH_LAUNCH_BATCHED(128, 10, 0);
-        } else {
-            if (a.acc_mode) BSH_LAUNCH_BATCHED(128, 13, 1); else BSH_LAUNCH_BATCHED(128, 13, 0);
-        }
+        if (a.lut) BSH_LAUNCH_NE(128, true); else BSH_LAUNCH_NE(128, false);
     } else {
-        if (small_n) {
-            if (a.acc_mode) BSH_LAUNCH_BATCHED(256, 10, 1); else BSH_LAUNCH_BATCHED(256, 10, 0);
-        } else {
-            if (a.acc_mode) BSH_LAUNCH_BATCHED(256, 13, 1); else BSH_LAUNCH_BATCHED(256, 13, 0);
-        }
+        if (a.lut) BSH_LAUNCH_NE(256, true); else BSH_LAUNCH_NE(256, false);
     }
+#undef BSH_LAUNCH_NE
+#undef BSH_LAUNCH_ACC
 #undef BSH_LAUNCH_BATCHED
 }
 

@@ -80,6 +80,13 @@ int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max,
     fp->eps = eZ + 1.0 + prod + cosulp + 1.0;
     fp->M = (int)std::ceil(2.0 * fp->eps) + 4;
     if (fp->M * 8 > (1 << fp->s_y)) return BSH_ERR_RANGE;
+    // slope margin of the reference-template test: |v(j) - v(j0 + 15)| <= 16 |D| 2^s_y for the
+    // block's templates, |D| <= |vn| + a_p |c|, |vn| <= (|vn_q| + 1) 2^-s_vn, |c| <= Om_max
+    // (a margin of a whole cell or more only sends every block to the two-ended test)
+    const double binpart = 16.0 * ap_max * Om_max * (1.0 + 1e-9) * u;
+    fp->mg_a = (int)std::min(std::ceil(binpart) + fp->M + 2, u);
+    if (fp->s_vn - fp->s_y - 4 < 0) return BSH_ERR_RANGE;
+    fp->mg_k = std::min(30, fp->s_vn - fp->s_y - 4);   // a smaller shift only rounds the margin up
     return BSH_OK;
 }
 
@@ -130,7 +137,8 @@ struct bsh_plan {
     int n = 0;
     std::vector<ProbHost> P;
     bsh_count_options opt{};
-    int mode = BSH_MODE_BATCHED;
+    int mode = BSH_MODE_BATCHED;           // BSH_MODE_LUT plans run as BATCHED with lut = 1
+    int lut = 0;
     int threads = 256, chunk = 128, ctas = 0, num_sms = 152;
     int wseg_max = 4, ot_max = 1, wrows = 1, smem = 0, cap = 0, top_k = 1000;
     int regions = 0, visits = 0, visit_cap = 0;
@@ -337,7 +345,8 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     if (!out) return BSH_ERR_ARG;
     *out = nullptr;
     if (!problems || n_problems < 1 || n_problems > MAX_PROBLEMS || !opt) return BSH_ERR_ARG;
-    if (opt->mode != BSH_MODE_BATCHED && opt->mode != BSH_MODE_PLAIN) return BSH_ERR_ARG;
+    if (opt->mode != BSH_MODE_BATCHED && opt->mode != BSH_MODE_PLAIN && opt->mode != BSH_MODE_LUT)
+        return BSH_ERR_ARG;
     if (opt->top_k < 1 || opt->top_k > 16384) return BSH_ERR_ARG;
     if (opt->threads != 0 && opt->threads != 128 && opt->threads != 256) return BSH_ERR_ARG;
     if (opt->sft_chunk != 0 && opt->sft_chunk != 64 && opt->sft_chunk != 128 && opt->sft_chunk != 256)
@@ -350,7 +359,8 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     bsh_plan* p = new bsh_plan();
     p->n = n_problems;
     p->opt = *opt;
-    p->mode = opt->mode;
+    p->mode = opt->mode == BSH_MODE_LUT ? BSH_MODE_BATCHED : opt->mode;
+    p->lut = opt->mode == BSH_MODE_LUT ? 1 : 0;
     p->top_k = opt->top_k;
     p->threads = opt->threads ? opt->threads : 256;
     p->chunk = opt->sft_chunk ? opt->sft_chunk : 128;
@@ -644,6 +654,7 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.mode = p->mode;
     a.wrows = p->wrows;
     a.acc_mode = p->acc_mode;
+    a.lut = p->lut;
     a.max_n = 0;
     for (auto& h : p->P) a.max_n = std::max(a.max_n, h.d.N);
     return a;
@@ -1040,9 +1051,10 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
         const int F2a = (int)std::llround(2.0 * d.F0) + 2 * j0;
         const int v0 = make_Z(F2a, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a, cq, fp));
         const int v1 = make_Z(F2a + 62, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a + 62, cq, fp));
+        const int vr = make_Z(F2a + 30, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a + 30, cq, fp));
         const uint32_t* row = row_bits + (size_t)e * d.W;
         const int pbase = pd.G0 + j0 - d.k_lo;
-        const int pos = pbase + (v0 >> fp.s_y);
+        const int pos = pbase + (vr >> fp.s_y);
         const double ap = h.ap[iap];
         auto exact_o = [&](int j) -> int {
             volatile double apc = ap * c;
@@ -1053,7 +1065,7 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
             volatile double xh = x + 0.5;
             return (int)((long long)std::floor(xh) - (long long)(pd.G0 + j0 + j));
         };
-        if (fp_fast(v0, v1, fp.s_y, fp.M) && (unsigned)pos <= (unsigned)pos_max) {
+        if (fp_fast_ref(vr, fp_margin(vq, fp), fp.s_y) && (unsigned)pos <= (unsigned)pos_max) {
             out[e] = row_window(row, pos);
             path[e] = 0;
         } else {

@@ -3,6 +3,7 @@
     python -m paper_1904_04873_gb300.experiments precision [--sky N]
     python -m paper_1904_04873_gb300.experiments batching [--patches P] [--steps K]
     python -m paper_1904_04873_gb300.experiments full [--sky N] [--injections M]
+    python -m paper_1904_04873_gb300.experiments lut [--sky N]
 
 precision  Half-bin f0 grid with forced exact ties: the fixed-point track of the
            batched kernels against the exact FP64 bins for every term of a sky
@@ -15,10 +16,16 @@ full       2 x 4000 SFTs, 10 Hz at 300 Hz, patches of 169 sky points, 8^3 binary
            templates, top-10000, stage-2 power sum; seeded injections placed on
            their exact tracks; recovery = a toplist entry within one grid step of
            the injection in every parameter.
+lut        Exact track against the look-up-table approximation of Sec. IV.B
+           (BSH_MODE_LUT) on the mid workload and on a fast-binary variant
+           (P = 1.5-3 d, a_p = 10-60 ls): number-count throughput of both, the
+           fraction of templates whose count changes, the change of s_H, and the
+           overlap of the per-patch toplists.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import sys
@@ -200,9 +207,68 @@ def full(n_sky: int = 100048, n_inj: int = 100, depth_amp: float = 0.5, top_k: i
             "efficiency_error": math.sqrt(E * (1 - E) / n_inj)}
 
 
+def _lut_case(pr, n_sky_dense: int, steps: int) -> dict:
+    import torch
+    dp = bsh.DeviceProblem(pr, w_dtype="f16")
+    dp.prepare()
+    out = {"modes": {}}
+    lists = {}
+    for name, mode in (("exact", bsh.MODE_BATCHED), ("lut", bsh.MODE_LUT)):
+        plan = bsh.Plan([dp], mode, top_k=pr.top_k)
+        tile = plan.autotune()
+        plan.number_count()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(steps):
+            plan.number_count()
+        e1.record()
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / steps
+        cands, n = plan.toplist()
+        assert bsh.sync_status() == bsh.OK
+        lists[name] = bsh.cands_to_numpy(cands, n)
+        out["modes"][name] = {"s_per_count": dt, "terms_per_s": pr.n_terms / dt, "tile": tile}
+        plan.close()
+    ov = [len(set(a["template_id"].tolist()) & set(b["template_id"].tolist())) / max(1, a.size)
+          for a, b in zip(lists["exact"], lists["lut"])]
+    out["toplist_overlap"] = {"mean": float(np.mean(ov)), "min": float(np.min(ov))}
+    out["lut_speedup"] = out["modes"]["exact"]["s_per_count"] / out["modes"]["lut"]["s_per_count"]
+    # dense counts of both on the first sky points
+    sub = dataclasses.replace(pr, sky=pr.sky[:n_sky_dense], patch_start=np.array([0, n_sky_dense]))
+    ds = bsh.DeviceProblem(sub, w_dtype="f16")
+    ds.prepare()
+    res = {}
+    for name, mode in (("exact", bsh.MODE_BATCHED), ("lut", bsh.MODE_LUT)):
+        plan = bsh.Plan([ds], mode, top_k=10)
+        gu, gw = plan.count_dense()
+        assert bsh.sync_status() == bsh.OK
+        res[name] = (gu[0].cpu().numpy(), gw[0].double().cpu().numpy())
+        plan.close()
+    p = math.exp(-pr.rho_th)
+    sig = np.sqrt(p * (1 - p) * ds.sum_w2.cpu().numpy())[:, None, None]
+    dsh = (res["lut"][1] - res["exact"][1]) / sig
+    out["dense"] = {"sky_points": n_sky_dense, "templates": int(res["exact"][0].size),
+                    "count_changed_fraction": float((res["lut"][0] != res["exact"][0]).mean()),
+                    "mean_unweighted_change": float((res["lut"][0] - res["exact"][0]).mean()),
+                    "s_h_change_mean": float(dsh.mean()), "s_h_change_rms": float(np.sqrt((dsh ** 2).mean())),
+                    "s_h_change_max_abs": float(np.abs(dsh).max())}
+    return out
+
+
+def lut(n_sky: int = 2000, steps: int = 3, n_sky_dense: int = 4) -> dict:
+    """Exact track vs the LUT approximation: throughput and count deviation."""
+    mid = synth.mid(n_sky=n_sky)
+    fast = synth.mid(n_sky=n_sky, a_p=np.linspace(10.0, 60.0, 32), P_days=np.linspace(1.5, 3.0, 32))
+    return {"mid": {"workload": f"mid: {mid.N} SFTs, {mid.S} sky points, 32^3 binaries (a_p 0.5-10 ls, "
+                                f"P 15-45 d), 90 f0"} | _lut_case(mid, n_sky_dense, steps),
+            "fast": {"workload": f"fast binaries: the mid construction with a_p 10-60 ls, P 1.5-3 d "
+                                 f"({fast.K} loaded bins)"} | _lut_case(fast, n_sky_dense, steps)}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["precision", "batching", "full"])
+    ap.add_argument("what", choices=["precision", "batching", "full", "lut"])
     ap.add_argument("--sky", type=int, default=0)
     ap.add_argument("--patches", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2)
@@ -218,6 +284,8 @@ def main(argv=None):
         r = precision(n_sky=a.sky or 2000)
     elif a.what == "batching":
         r = batching(n_patch=a.patches, steps=a.steps)
+    elif a.what == "lut":
+        r = lut(n_sky=a.sky or 2000)
     else:
         r = full(n_sky=a.sky or 100048, n_inj=a.injections, depth_amp=a.amp, n_f0=a.f0)
     print(json.dumps(r))

@@ -290,7 +290,8 @@ TINY_INJECTION = dict(sky=3, ap_index=1, Om_index=1, T_index=1, f0_index=45, exc
 
 def mid(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32, n_T: int = 32,
         half_bin: bool = False, seed: int = SEED_NOISE, patch_size: int = 50, top_k: int = 1000,
-        orbit_only: bool = False, sky: Optional[np.ndarray] = None, a_p: Optional[np.ndarray] = None) -> Problem:
+        orbit_only: bool = False, sky: Optional[np.ndarray] = None, a_p: Optional[np.ndarray] = None,
+        P_days: Optional[np.ndarray] = None) -> Problem:
     """Plain method, mid: 2 detectors x 2000 SFTs of 900 s over 1 yr (random
     starts), Gaussian noise with a 1-1.5 S_n ratio between detectors, 0.1 Hz
     band at 200 Hz, 2000 sky points in patches of 50, a_p 0.5-10 ls (32),
@@ -300,9 +301,11 @@ def mid(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,
         sky = fibonacci_sky(n_sky)
     if a_p is None:
         a_p = np.linspace(0.5, 10.0, n_ap)
+    if P_days is None:
+        P_days = np.linspace(15.0, 45.0, n_P)
     return make_problem("mid", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=900.0, span=YEAR_SID,
                         random_times=True, f_lo=200.0, n_f0=90, half_bin=half_bin, sky=sky,
-                        patch_size=patch_size, a_p=a_p, P_days=np.linspace(15.0, 45.0, n_P),
+                        patch_size=patch_size, a_p=a_p, P_days=P_days,
                         n_T=n_T, power_kind="gauss", seed=seed, top_k=top_k, orbit_only=orbit_only)
 
 
