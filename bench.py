@@ -166,27 +166,35 @@ class ClockSampler:
         return out
 
 
-def profiled_traffic(kind: str):
-    """DRAM bytes per count launch from the committed ncu summary, if it was taken
-    on the current kernel sources (same short hash) and on this workload."""
+def kernel_sha() -> str:
+    """Short hash of the count kernel's sources (matches the ncu summaries' stamp)."""
     import hashlib
-    if kind != "mid":
-        return None, None
     src = os.path.join(ROOT, "paper_1904_04873_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
         h.update(open(os.path.join(src, f), "rb").read())
-    sha = h.hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "count_batched_mid.md")
+    return h.hexdigest()[:16]
+
+
+def profile_value(name: str, key: str):
+    """A figure recorded in a committed ncu summary, with its source; None when the
+    summary is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None, None
-    vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_launch:",
-                                                                          "kernel_source_sha256_16:")))
-    if vals.get("kernel_source_sha256_16", "").strip() != sha:
-        return None, "profiles/count_batched_mid.md (stale: kernel changed since)"
-    return float(vals["traffic_bytes_per_launch"]), "profiles/count_batched_mid.md"
+    vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith((key + ":", "kernel_source_sha256_16:")))
+    if vals.get("kernel_source_sha256_16", "").strip() != kernel_sha() or key not in vals:
+        return None, f"profiles/{name} (stale: kernel changed since)"
+    return float(vals[key]), f"profiles/{name}"
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per count launch from the committed ncu summary of this workload."""
+    if kind != "mid":
+        return None, None
+    return profile_value("count_batched_mid.md", "traffic_bytes_per_launch")
 
 
 def measured_peaks():
@@ -432,11 +440,15 @@ def main():
                 "terms_per_s": count_rate, "count_ms": count_s * 1e3}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
-    # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the
-    # 3.55 thread instructions per term measured by ncu (profiles/count_batched_small_full.md)
-    ipt = 3.55
-    roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / ipt, "instr_per_term": ipt,
-                       "frac": count_rate / (n_sm * 128.0 * f_max / ipt)}
+    # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the thread
+    # instructions per term that ncu measured for this kernel variant
+    ipt, ipt_src = profile_value("count_batched_small_full.md",
+                                 "lut_instr_per_term" if args.track == "lut" else "instr_per_term")
+    if ipt:
+        roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / ipt, "instr_per_term": ipt,
+                           "frac": count_rate / (n_sm * 128.0 * f_max / ipt), "source": ipt_src}
+    else:
+        roofline["alu"] = {"ceiling_terms_per_s": None, "instr_per_term": None, "frac": None, "source": ipt_src}
 
     cpu = None
     if not args.no_cpu and rank == 0:
