@@ -25,8 +25,9 @@
  *   - Frequencies are bin numbers F = f * T_c (Eq. (33): delta f = 1/T_c).
  *   - Template order inside a problem: id = ((s * B + b) * n_f0 + j) with
  *     F_j = F0 + j and the binary index
- *       b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap,
- *     where n_kap (n_eta) counts as 1 when the problem gives no kappa (eta).
+ *       b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap
+ *     for a grid, where n_kap (n_eta) counts as 1 when the problem gives no
+ *     kappa (eta), or b = the entry of an explicit bank (bank_orbit, bank_ap).
  *   - Track of a template at SFT i (Eq. (14) and (15) times T_c):
  *       k_i = floor(F (1 + v_i.n - a_p Omega g_i) + 1/2),
  *       g_i = cos(phi) + kappa cos(2 phi) + eta sin(2 phi),
@@ -169,6 +170,14 @@ typedef struct bsh_problem {
     const double* kappa;       /* [n_kappa] e cos(omega), |kappa| <= 0.5 */
     int n_eta;
     const double* eta;         /* [n_eta] e sin(omega), |eta| <= 0.5 */
+    /* explicit binary bank, HOST arrays (copied by bsh_plan_create), for template banks   */
+    /* whose spacing varies over the parameter space (Eq. (30)-(32)): n_orbit > 0 selects */
+    /* it and the a_p / Omega / T_asc / kappa / eta grid above is not read.                */
+    int n_orbit;
+    const double* orbit;       /* [n_orbit][4]: Omega (> 0), t_asc, kappa, eta (|.| <= 0.5) */
+    int n_bank;                /* B: binary templates, <= 2^30 */
+    const int32_t* bank_orbit; /* [B] orbit row of binary template b, non-decreasing in b */
+    const double* bank_ap;     /* [B] a_p of binary template b (light-seconds, >= 0) */
 } bsh_problem;
 
 typedef struct bsh_count_options {
@@ -307,6 +316,43 @@ int bsh_track_bins(bsh_plan* plan, int problem, const int64_t* ids, int n, int32
 /* ------------------------------------------------------------------------ */
 int bsh_debug_track_windows(const bsh_problem* host_problem, const int32_t* query /*[count][4]: s,b,i,j0*/,
                             int count, const uint32_t* row_bits, uint32_t* out, int32_t* path);
+
+/* ------------------------------------------------------------------------ */
+/* Binary template bank, Sec. V.B, Eq. (30)-(32).  HOST only, no CUDA call.   */
+/*                                                                          */
+/* bsh_binary_resolution: the spacings at (f, a_p, Omega) for the mismatch   */
+/*   parameters m_a, m_Om, m_t (f in Hz, T_c and T_obs in s, a_p in          */
+/*   light-seconds, Omega in rad/s):                                         */
+/*     d_ap = sqrt(6 m_a) / (pi T_c f Omega)                                 */
+/*     d_Om = sqrt(72 m_Om) / (pi T_c f a_p Omega T_obs)                     */
+/*     d_t  = sqrt(6 m_t) / (pi T_c f a_p Omega^2)                           */
+/* bsh_template_bank: a bank over a_p in [ap_min, ap_max], P in [P_min,       */
+/*   P_max] and t_asc within half a period of t_mid (Eq. (35)), as orbit rows */
+/*   and (row, a_p) entries in the layout of bsh_problem's explicit bank:     */
+/*   Omega from 2 pi / P_max upwards, each step d_Om at ap_max, until past    */
+/*   2 pi / P_min; at each Omega, a_p from ap_min in steps of d_ap(Omega)     */
+/*   up to ap_max, cut into blocks whose largest / smallest a_p ratio is at   */
+/*   most ap_block; each block gets t_asc values from t_mid - P/2 in steps of */
+/*   d_t at the block's largest a_p, below t_mid + P/2.  Every spacing is the */
+/*   smallest the metric asks for over the cell it covers.  Call with NULL    */
+/*   arrays for the sizes (n_orbit, n_bank), then with arrays of at least     */
+/*   those capacities; BSH_ERR_WORKSPACE if a capacity is too small,          */
+/*   BSH_ERR_RANGE if P_min <= T_c or the bank would exceed 2^30 entries.     */
+/* ------------------------------------------------------------------------ */
+typedef struct bsh_bank_spec {
+    double f;                  /* frequency (Hz) the spacings use: the band's highest */
+    double T_c, T_obs;         /* coherence time and observation time (s) */
+    double t_mid;              /* centre of the t_asc range (s) */
+    double ap_min, ap_max;     /* light-seconds, 0 < ap_min <= ap_max */
+    double P_min, P_max;       /* orbital period (s), T_c < P_min <= P_max */
+    double m_a, m_Om, m_t;     /* mismatch parameters (> 0) */
+    double ap_block;           /* a_p ratio sharing one t_asc grid (>= 1) */
+} bsh_bank_spec;
+
+int bsh_binary_resolution(double f, double T_c, double T_obs, double a_p, double Omega, double m_a, double m_Om,
+                          double m_t, double* d_ap, double* d_Om, double* d_t);
+int bsh_template_bank(const bsh_bank_spec* spec, int* n_orbit, double* orbit, int orbit_cap, int* n_bank,
+                      int32_t* bank_orbit, double* bank_ap, int bank_cap);
 
 /* ------------------------------------------------------------------------ */
 /* Stage-2 power sum that allocates nothing.  The paper has no counterpart:  */

@@ -61,6 +61,8 @@ class Problem(ctypes.Structure):
         ("rho_th", ctypes.c_double), ("tie_band", ctypes.c_double),
         ("n_kap", ctypes.c_int), ("kap", ctypes.c_void_p), ("n_eta", ctypes.c_int), ("eta", ctypes.c_void_p),
         ("lut_block", ctypes.c_int),
+        ("n_orbit", ctypes.c_int), ("orbit", ctypes.c_void_p), ("n_bank", ctypes.c_int64),
+        ("bank_orbit", ctypes.c_void_p), ("bank_ap", ctypes.c_void_p),
     ]
 
 
@@ -202,7 +204,12 @@ class OracleProblem:
     """Holds contiguous arrays alive for the ctypes struct."""
 
     def __init__(self, *, bits, w, v, t, F0, n_f0, sky, a_p, Omega, T_asc, k_lo, K, rho=None,
-                 rho_th: float = 1.6, tie_band: float = TIE_BAND, kappa=None, eta=None, lut_block: int = 0):
+                 rho_th: float = 1.6, tie_band: float = TIE_BAND, kappa=None, eta=None, lut_block: int = 0,
+                 orbit=None, bank_orbit=None, bank_ap=None):
+        """Binary templates: the a_p x Omega x t_asc (x kappa x eta) grid, or with
+        ``orbit`` ([R][4]: Omega, t_asc, kappa, eta) an explicit bank where template b
+        has a_p = bank_ap[b] on orbit row bank_orbit[b] (then a_p / Omega / T_asc are
+        not used and may be empty)."""
         self.bits = _c(bits, np.uint32)
         self.w = _c(w, np.float64)
         self.v = _c(v, np.float64)
@@ -219,6 +226,11 @@ class OracleProblem:
         nk = 1 if self.kap is None else self.kap.size
         ne = 1 if self.eta is None else self.eta.size
         self.B = self.ap.size * self.Om.size * self.n_T * nk * ne
+        self.orbit = None if orbit is None else _c(orbit, np.float64).reshape(-1, 4)
+        self.bank_orbit = None if bank_orbit is None else _c(bank_orbit, np.int32)
+        self.bank_ap = None if bank_ap is None else _c(bank_ap, np.float64)
+        if self.orbit is not None:
+            self.B = self.bank_ap.size
         self.S = self.sky.shape[0]
         self.n_f0 = int(n_f0)
         self.N = N
@@ -233,7 +245,12 @@ class OracleProblem:
                          kap=None if self.kap is None else self.kap.ctypes.data,
                          n_eta=0 if self.eta is None else self.eta.size,
                          eta=None if self.eta is None else self.eta.ctypes.data,
-                         lut_block=int(lut_block))
+                         lut_block=int(lut_block),
+                         n_orbit=0 if self.orbit is None else self.orbit.shape[0],
+                         orbit=None if self.orbit is None else self.orbit.ctypes.data,
+                         n_bank=0 if self.orbit is None else self.bank_ap.size,
+                         bank_orbit=None if self.orbit is None else self.bank_orbit.ctypes.data,
+                         bank_ap=None if self.orbit is None else self.bank_ap.ctypes.data)
 
     def count_one(self, s: int, b: int, j: int):
         nu, nw, nt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()

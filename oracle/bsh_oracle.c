@@ -271,6 +271,13 @@ typedef struct {
     int n_eta;
     const double* eta;    /* [n_eta] e sin(omega), or NULL with n_eta = 0 */
     int lut_block;        /* 0: exact track; L > 0: look-up-table approximation, blocks of L f0 */
+    /* explicit binary bank: n_orbit > 0 selects it and the grid above is ignored;
+       binary template b has a_p = bank_ap[b] and the orbit row bank_orbit[b] */
+    int n_orbit;
+    const double* orbit;      /* [n_orbit][4]: Omega, t_asc, kappa, eta */
+    int64_t n_bank;
+    const int32_t* bank_orbit;/* [n_bank] */
+    const double* bank_ap;    /* [n_bank] */
 } orc_problem;
 
 /* Look-up-table approximation of stage 1 (Sec. IV.B): the modulation F D of  */
@@ -291,6 +298,15 @@ static int lut_ref(const orc_problem* pr, int j) {
 
 static void template_params(const orc_problem* pr, int64_t b, double* ap, double* Om, double* Ta,
                             double* kap, double* eta) {
+    if (pr->n_orbit > 0) {
+        const double* o = pr->orbit + 4 * (size_t)pr->bank_orbit[b];
+        *ap = pr->bank_ap[b];
+        *Om = o[0];
+        *Ta = o[1];
+        *kap = o[2];
+        *eta = o[3];
+        return;
+    }
     int nk = pr->n_kap > 0 ? pr->n_kap : 1;
     int ne = pr->n_eta > 0 ? pr->n_eta : 1;
     int64_t iap = b % pr->n_ap;
@@ -369,8 +385,9 @@ int orc_count_one(const orc_problem* pr, int s, int64_t b, int j,
 int orc_count_dense(const orc_problem* pr, int s_begin, int s_end,
                     int32_t* n_unw, double* n_w, int32_t* n_tie,
                     int32_t* unw_lo, int32_t* unw_hi, double* w_lo, double* w_hi) {
-    int64_t B = (int64_t)pr->n_ap * pr->n_Om * pr->n_T * (pr->n_kap > 0 ? pr->n_kap : 1) *
-                (pr->n_eta > 0 ? pr->n_eta : 1);
+    int64_t B = pr->n_orbit > 0 ? pr->n_bank
+                                : (int64_t)pr->n_ap * pr->n_Om * pr->n_T * (pr->n_kap > 0 ? pr->n_kap : 1) *
+                                      (pr->n_eta > 0 ? pr->n_eta : 1);
     size_t idx = 0;
     for (int s = s_begin; s < s_end; ++s)
         for (int64_t b = 0; b < B; ++b)

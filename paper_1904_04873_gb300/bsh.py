@@ -47,11 +47,15 @@ class Problem(ctypes.Structure):
         ("rho_th", ctypes.c_double),
         ("n_kappa", ctypes.c_int), ("kappa", ctypes.c_void_p),
         ("n_eta", ctypes.c_int), ("eta", ctypes.c_void_p),
+        ("n_orbit", ctypes.c_int), ("orbit", ctypes.c_void_p),
+        ("n_bank", ctypes.c_int), ("bank_orbit", ctypes.c_void_p), ("bank_ap", ctypes.c_void_p),
     ]
 
 
 def _ecc_fields(pr, keep: dict) -> dict:
-    """n_kappa / kappa / n_eta / eta of a problem (HOST arrays kept alive in ``keep``)."""
+    """The eccentric grid (n_kappa / kappa / n_eta / eta) and the explicit bank
+    (n_orbit / orbit / n_bank / bank_orbit / bank_ap) of a problem, as HOST
+    arrays kept alive in ``keep``."""
     out = {}
     for name in ("kappa", "eta"):
         a = getattr(pr, name, None)
@@ -60,6 +64,16 @@ def _ecc_fields(pr, keep: dict) -> dict:
         else:
             keep[name] = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
             out["n_" + name], out[name] = keep[name].size, keep[name].ctypes.data
+    orbit = getattr(pr, "orbit", None)
+    if orbit is None:
+        out.update(n_orbit=0, orbit=None, n_bank=0, bank_orbit=None, bank_ap=None)
+    else:
+        keep["orbit"] = np.ascontiguousarray(orbit, dtype=np.float64).reshape(-1, 4)
+        keep["bank_orbit"] = np.ascontiguousarray(pr.bank_orbit, dtype=np.int32).reshape(-1)
+        keep["bank_ap"] = np.ascontiguousarray(pr.bank_ap, dtype=np.float64).reshape(-1)
+        out.update(n_orbit=keep["orbit"].shape[0], orbit=keep["orbit"].ctypes.data,
+                   n_bank=keep["bank_ap"].size, bank_orbit=keep["bank_orbit"].ctypes.data,
+                   bank_ap=keep["bank_ap"].ctypes.data)
     return out
 
 
@@ -115,7 +129,15 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_binary_resolution": (ctypes.c_int, [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3),
+    "bsh_template_bank": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
+
+
+class BankSpec(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("f", "T_c", "T_obs", "t_mid", "ap_min", "ap_max", "P_min", "P_max",
+                                               "m_a", "m_Om", "m_t", "ap_block")]
 
 
 def lib():
@@ -395,3 +417,25 @@ def debug_track_windows(pr, queries: np.ndarray, rows: np.ndarray):
     _check(lib().bsh_debug_track_windows(ctypes.byref(d), q.ctypes.data, n, rows.ctypes.data, out.ctypes.data,
                                          path.ctypes.data), "bsh_debug_track_windows")
     return out, path
+
+
+def binary_resolution(f, T_c, T_obs, a_p, Omega, m_a, m_Om, m_t):
+    """bsh_binary_resolution: (d_ap, d_Om, d_t) of Eq. (30)-(32)."""
+    out = [ctypes.c_double() for _ in range(3)]
+    _check(lib().bsh_binary_resolution(f, T_c, T_obs, a_p, Omega, m_a, m_Om, m_t, *[ctypes.byref(o) for o in out]),
+           "bsh_binary_resolution")
+    return tuple(o.value for o in out)
+
+
+def template_bank(**spec):
+    """bsh_template_bank: (orbit [R][4], bank_orbit [B], bank_ap [B]) for a BankSpec."""
+    sp = BankSpec(**{k: float(v) for k, v in spec.items()})
+    nr, nb = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bsh_template_bank(ctypes.byref(sp), ctypes.byref(nr), None, 0, ctypes.byref(nb), None, None, 0),
+           "bsh_template_bank")
+    orbit = np.zeros((nr.value, 4))
+    bo = np.zeros(nb.value, np.int32)
+    ba = np.zeros(nb.value)
+    _check(lib().bsh_template_bank(ctypes.byref(sp), ctypes.byref(nr), orbit.ctypes.data, orbit.shape[0],
+                                   ctypes.byref(nb), bo.ctypes.data, ba.ctypes.data, bo.size), "bsh_template_bank")
+    return orbit, bo, ba

@@ -79,17 +79,15 @@ struct ProbDev {
     double* c64;              // [nOT][Np]
     float* w32;               // [S][Np]   (batched mode)
     double* w64;              // [S][Np]   (plain mode)
-    const double* a_p;        // [n_ap]
-    const int32_t* ap_q;      // [n_ap]
-    const double* Om;         // [n_Om]
-    const double* Tasc;       // [n_Om * n_T]
-    const double* kap;        // [n_kap] or NULL (circular)
-    const double* eta;        // [n_eta] or NULL (circular)
+    // binary templates: orbit rows and, per template b, its row, a_p and fixed-point a_p
+    const double* orb;        // [nOT][4] Omega, t_asc, kappa, eta
+    const int32_t* brow;      // [B] orbit row of template b (non-decreasing in b)
+    const double* bap;        // [B] a_p of template b
+    const int32_t* bapq;      // [B] round(a_p 2^s_a)
     const int64_t* patch_start;  // [n_patch + 1]
     const int32_t* patch_of_s;   // [S]
     // sizes
-    int N, Np, K, W, k_lo, n_f0, S, n_ap, n_Om, n_T, nOT, B, n_patch, w_dtype;
-    int n_kap, n_eta;         // >= 1 (1 with a NULL array: the value 0)
+    int N, Np, K, W, k_lo, n_f0, S, nOT, B, n_patch, w_dtype;
     double F0;                // first template (bins)
     int G0;                   // floor(F0)
     int JB;                   // valid templates per f0 block (<= 32)

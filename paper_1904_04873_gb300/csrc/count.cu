@@ -157,8 +157,8 @@ __device__ __forceinline__ ItemCtx item_ctx(const CountArgs& a, const Item& it, 
     c.pbase = Gj0 - P.k_lo - 32 * c.c0;
     const int b0 = it.bt * THREADS;
     const int b1 = imin(b0 + THREADS, P.B) - 1;
-    c.ot0 = b0 / P.n_ap;
-    c.nrows = b1 / P.n_ap - c.ot0 + 1;
+    c.ot0 = P.brow[b0];
+    c.nrows = P.brow[b1] - c.ot0 + 1;
     c.F2a = (int)llrint(2.0 * P.F0) + 2 * c.j0;
     c.F2r = c.F2a + 2 * ((c.jb - 1) / 2);   // 2 F of the block's middle template (LUT reference)
     const int patch = P.patch_of_s[it.s];
@@ -217,10 +217,8 @@ __device__ __forceinline__ uint32_t slow_window_exact(const ProbDev& P, int v0, 
             const double* v = P.v + 3 * (size_t)i;
             const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])),
                                         __dmul_rn(v[2], n[2]));
-            const int iap = b % P.n_ap;
-            const int ot = b / P.n_ap;
-            const double c = P.c64[(size_t)ot * P.Np + i];
-            D = __dsub_rn(vn, __dmul_rn(P.a_p[iap], c));
+            const double c = P.c64[(size_t)P.brow[b] * P.Np + i];
+            D = __dsub_rn(vn, __dmul_rn(P.bap[b], c));
             have = true;
         }
         const double F = P.F0 + (double)(j0 + j);
@@ -241,8 +239,8 @@ __device__ __noinline__ uint32_t slow_window_lut(const ProbDev& P, int pbase, in
     const double* n = P.sky + 3 * (size_t)s;
     const double* v = P.v + 3 * (size_t)i;
     const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])), __dmul_rn(v[2], n[2]));
-    const double c = P.c64[(size_t)(b / P.n_ap) * P.Np + i];
-    const double D = __dsub_rn(vn, __dmul_rn(P.a_p[b % P.n_ap], c));
+    const double c = P.c64[(size_t)P.brow[b] * P.Np + i];
+    const double D = __dsub_rn(vn, __dmul_rn(P.bap[b], c));
     const double F = P.F0 + (double)jr;
     const double x = __dadd_rn(F, __dmul_rn(F, D));
     const int o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)(P.G0 + jr));
@@ -426,14 +424,13 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         const ProbDev& P = a.probs[cur.q];
         const int b = cur.bt * THREADS + tid;
         const bool bvalid = b < P.B;
-        const int iap = bvalid ? b % P.n_ap : 0;
         const int b_w0 = cur.bt * THREADS + warp * 32;          // first binary of this warp
-        const int otw0 = imin(b_w0, P.B - 1) / P.n_ap;         // first Omega-T row of this warp
-        const int otw1 = imin(b_w0 + 31, P.B - 1) / P.n_ap;
+        const int otw0 = P.brow[imin(b_w0, P.B - 1)];           // first orbit row of this warp
+        const int otw1 = P.brow[imin(b_w0 + 31, P.B - 1)];
         const int nrw = otw1 - otw0 + 1;                        // rows this warp needs (<= wrows)
-        const int ot = bvalid ? b / P.n_ap - otw0 : 0;
+        const int ot = bvalid ? P.brow[b] - otw0 : 0;
         const int orow0 = otw0 - cur.ot0;                       // their offset in the CTA's staged rows
-        const int apq = bvalid ? P.ap_q[iap] : 0;
+        const int apq = bvalid ? P.bapq[b] : 0;
         const int s_y = P.fp.s_y, M = P.fp.M;
         const int wseg = a.wseg_max;
         const int pos_max = 32 * wseg - 33;
@@ -674,8 +671,8 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
 #pragma unroll
         for (int j = 0; j < JW; ++j) { accw[j] = 0.0; cnt[j] = 0u; }
         if (bvalid) {
-            const int iap = b % P.n_ap, otg = b / P.n_ap;
-            const double ap = P.a_p[iap];
+            const int otg = P.brow[b];
+            const double ap = P.bap[b];
             const double* n = P.sky + 3 * (size_t)cur.s;
             for (int i = 0; i < P.N; ++i) {
                 const double* v = P.v + 3 * (size_t)i;

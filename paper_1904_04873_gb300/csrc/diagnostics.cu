@@ -26,17 +26,17 @@ __global__ void precision_kernel(const ProbDev* probs, int s_begin, int s_end, u
         const long long r = e % per;
         const int b = (int)(r / P.N);
         const int i = (int)(r % P.N);
-        const int iap = b % P.n_ap, ot = b / P.n_ap;
+        const int ot = P.brow[b];
         const double vn = vn_of(P, s, i);
         const double c = P.c64[(size_t)ot * P.Np + i];
-        const double ap = P.a_p[iap];
+        const double ap = P.bap[b];
         const double D = __dsub_rn(vn, __dmul_rn(ap, c));
         // single precision evaluation of the same expression
         const float vn32 = (float)vn, c32 = (float)c, ap32 = (float)ap;
         const float D32 = __fsub_rn(vn32, __fmul_rn(ap32, c32));
         const int vq = P.vn_q[(size_t)s * P.Np + i];
         const int cq = P.c_q[(size_t)ot * P.Np + i];
-        const int apq = P.ap_q[iap];
+        const int apq = P.bapq[b];
         const int cell = 1 << P.fp.s_y;
         for (int j = 0; j < P.n_f0; ++j) {
             const double F = P.F0 + (double)j;
@@ -81,10 +81,11 @@ __global__ void bins_kernel(const ProbDev* probs, const int64_t* ids, int n, int
     const long long rem = id % per_s;
     const int b = (int)(rem / P.n_f0);
     const int j = (int)(rem % P.n_f0);
-    const int iap = b % P.n_ap, ot = b / P.n_ap;
+    const int ot = P.brow[b];
+    const double ap = P.bap[b];
     const double F = P.F0 + (double)j;
     for (int i = lane; i < P.N; i += 32) {
-        const double D = __dsub_rn(vn_of(P, s, i), __dmul_rn(P.a_p[iap], P.c64[(size_t)ot * P.Np + i]));
+        const double D = __dsub_rn(vn_of(P, s, i), __dmul_rn(ap, P.c64[(size_t)ot * P.Np + i]));
         const double x = __dadd_rn(F, __dmul_rn(F, D));
         bins[(size_t)e * P.N + i] = (int32_t)floor(__dadd_rn(x, 0.5));
     }

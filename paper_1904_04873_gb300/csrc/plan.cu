@@ -92,43 +92,65 @@ int choose_fixed_point(double F_max, double v_max, double ap_max, double Om_max,
 
 struct ProbHost {
     bsh_problem d;                         // caller descriptor (device pointers)
-    std::vector<double> ap, Om, Tasc, kap, eta;   // kap / eta empty: circular orbits
+    std::vector<double> orb;               // [nOT][4] Omega, t_asc, kappa, eta
+    std::vector<int32_t> brow;             // [B] orbit row of each binary template
+    std::vector<double> bap;               // [B] a_p of each binary template
+    std::vector<int32_t> bapq;             // [B] fixed-point a_p (set with the scales)
     std::vector<int64_t> ps;
-    std::vector<int32_t> patch_of_s, ap_q;
+    std::vector<int32_t> patch_of_s;
     ProbDev pd;                            // filled at create (sizes) and bind (pointers)
-    size_t off_ap, off_apq, off_Om, off_Tasc, off_kap, off_eta, off_ps, off_pos, off_vnq, off_cq, off_c64, off_w;
+    size_t off_orb, off_brow, off_bap, off_bapq, off_ps, off_pos, off_vnq, off_cq, off_c64, off_w;
 };
 
-// Orbit rows of a problem: (Omega, t_asc) pairs times the eccentric grid.
-long long orbit_rows(const bsh_problem& d) {
-    return (long long)d.n_Om * d.n_T * std::max(1, d.n_kappa) * std::max(1, d.n_eta);
+bool uses_bank(const bsh_problem& d) { return d.n_orbit > 0; }
+
+// Binary templates of a problem as orbit rows plus (row, a_p) per template: the explicit bank
+// as given, or the grid written out in its template order
+// b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap.
+void expand_binaries(ProbHost& h, const bsh_problem& d) {
+    h.orb.clear();
+    h.brow.clear();
+    h.bap.clear();
+    if (uses_bank(d)) {
+        h.orb.assign(d.orbit, d.orbit + 4 * (size_t)d.n_orbit);
+        h.brow.assign(d.bank_orbit, d.bank_orbit + d.n_bank);
+        h.bap.assign(d.bank_ap, d.bank_ap + d.n_bank);
+        return;
+    }
+    const int nk = std::max(1, d.n_kappa), ne = std::max(1, d.n_eta);
+    for (int iOm = 0; iOm < d.n_Om; ++iOm)
+        for (int iT = 0; iT < d.n_T; ++iT)
+            for (int ik = 0; ik < nk; ++ik)
+                for (int ie = 0; ie < ne; ++ie) {
+                    h.orb.push_back(d.Omega[iOm]);
+                    h.orb.push_back(d.T_asc[(size_t)iOm * d.n_T + iT]);
+                    h.orb.push_back(d.n_kappa > 0 ? d.kappa[ik] : 0.0);
+                    h.orb.push_back(d.n_eta > 0 ? d.eta[ie] : 0.0);
+                }
+    const int rows = (int)(h.orb.size() / 4);
+    h.brow.reserve((size_t)rows * d.n_ap);
+    h.bap.reserve((size_t)rows * d.n_ap);
+    for (int r = 0; r < rows; ++r)
+        for (int k = 0; k < d.n_ap; ++k) {
+            h.brow.push_back(r);
+            h.bap.push_back(d.a_p[k]);
+        }
 }
 
-// Largest |kappa| and |eta| of the grid (0 when absent).
-double ecc_bound(const bsh_problem& d) {
-    double km = 0.0, em = 0.0;
-    for (int k = 0; k < d.n_kappa; ++k) km = std::max(km, std::fabs(d.kappa[k]));
-    for (int k = 0; k < d.n_eta; ++k) em = std::max(em, std::fabs(d.eta[k]));
-    return km + em;
+// Binary templates of a problem (grid size or bank size).
+long long binary_count(const bsh_problem& d) {
+    if (uses_bank(d)) return d.n_bank;
+    return (long long)d.n_ap * d.n_Om * d.n_T * std::max(1, d.n_kappa) * std::max(1, d.n_eta);
 }
 
-void copy_grid(ProbHost& h, const bsh_problem& d) {
-    h.ap.assign(d.a_p, d.a_p + d.n_ap);
-    h.Om.assign(d.Omega, d.Omega + d.n_Om);
-    h.Tasc.assign(d.T_asc, d.T_asc + (size_t)d.n_Om * d.n_T);
-    if (d.n_kappa > 0) h.kap.assign(d.kappa, d.kappa + d.n_kappa);
-    else h.kap.clear();
-    if (d.n_eta > 0) h.eta.assign(d.eta, d.eta + d.n_eta);
-    else h.eta.clear();
-}
-
-// |Omega g| bound over the orbit rows, g of Eq. (14).
-double c_bound(const ProbHost& h) {
-    double Om_max = 0.0, km = 0.0, em = 0.0;
-    for (double o : h.Om) Om_max = std::max(Om_max, o);
-    for (double k : h.kap) km = std::max(km, std::fabs(k));
-    for (double e : h.eta) em = std::max(em, std::fabs(e));
-    return Om_max * (1.0 + km + em);
+// Largest a_p and bound on |Omega g| = |c| over the orbit rows (g of Eq. (14)).
+void binary_bounds(const ProbHost& h, double* ap_max, double* c_max) {
+    double a = 0.0, c = 0.0;
+    for (double x : h.bap) a = std::max(a, x);
+    for (size_t r = 0; r < h.orb.size() / 4; ++r)
+        c = std::max(c, h.orb[4 * r] * (1.0 + std::fabs(h.orb[4 * r + 2]) + std::fabs(h.orb[4 * r + 3])));
+    *ap_max = a;
+    *c_max = c;
 }
 
 }  // namespace
@@ -189,7 +211,22 @@ int validate_problem(const bsh_problem& d) {
     if (reinterpret_cast<uintptr_t>(d.bits) % 16 != 0) return BSH_ERR_ARG;
     if (d.w_dtype < BSH_F64 || d.w_dtype > BSH_BF16) return BSH_ERR_ARG;
     if (d.n_f0 <= 0 || d.S <= 0 || d.n_patch <= 0 || !d.patch_start) return BSH_ERR_ARG;
-    if (d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || !d.a_p || !d.Omega || !d.T_asc) return BSH_ERR_ARG;
+    if (uses_bank(d)) {
+        if (d.n_bank <= 0 || !d.orbit || !d.bank_orbit || !d.bank_ap) return BSH_ERR_ARG;
+        if (d.n_bank > (1 << 30)) return BSH_ERR_RANGE;
+        for (int r = 0; r < d.n_orbit; ++r) {
+            const double* o = d.orbit + 4 * (size_t)r;
+            if (!finite_pos(o[0]) || !std::isfinite(o[1]) || !(std::fabs(o[2]) <= 0.5) || !(std::fabs(o[3]) <= 0.5))
+                return BSH_ERR_ARG;
+        }
+        for (int b = 0; b < d.n_bank; ++b) {
+            if (d.bank_orbit[b] < 0 || d.bank_orbit[b] >= d.n_orbit) return BSH_ERR_ARG;
+            if (b > 0 && d.bank_orbit[b] < d.bank_orbit[b - 1]) return BSH_ERR_ARG;
+            if (!(d.bank_ap[b] >= 0.0) || !std::isfinite(d.bank_ap[b])) return BSH_ERR_ARG;
+        }
+    } else if (d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || !d.a_p || !d.Omega || !d.T_asc) {
+        return BSH_ERR_ARG;
+    }
     if (!finite_pos(d.v_max) || !std::isfinite(d.F0) || d.F0 <= 0.0) return BSH_ERR_ARG;
     const double F2 = 2.0 * d.F0;
     if (F2 != std::floor(F2) || F2 + 2.0 * (d.n_f0 + 64) > 2147483000.0) return BSH_ERR_ARG;
@@ -197,6 +234,7 @@ int validate_problem(const bsh_problem& d) {
     if (d.patch_start[0] != 0 || d.patch_start[d.n_patch] != d.S) return BSH_ERR_ARG;
     for (int p = 0; p < d.n_patch; ++p)
         if (d.patch_start[p + 1] < d.patch_start[p]) return BSH_ERR_ARG;
+    if (uses_bank(d)) return BSH_OK;
     for (int k = 0; k < d.n_ap; ++k)
         if (!(d.a_p[k] >= 0.0) || !std::isfinite(d.a_p[k])) return BSH_ERR_ARG;
     for (int k = 0; k < d.n_Om; ++k)
@@ -209,6 +247,7 @@ int validate_problem(const bsh_problem& d) {
         if (!(std::fabs(d.kappa[k]) <= 0.5)) return BSH_ERR_ARG;
     for (int k = 0; k < d.n_eta; ++k)
         if (!(std::fabs(d.eta[k]) <= 0.5)) return BSH_ERR_ARG;
+    if (binary_count(d) > (1LL << 30)) return BSH_ERR_RANGE;
     return BSH_OK;
 }
 
@@ -222,14 +261,9 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
     pd.k_lo = d.k_lo;
     pd.n_f0 = d.n_f0;
     pd.S = d.S;
-    pd.n_ap = d.n_ap;
-    pd.n_Om = d.n_Om;
-    pd.n_T = d.n_T;
-    pd.n_kap = std::max(1, (int)h.kap.size());
-    pd.n_eta = std::max(1, (int)h.eta.size());
-    const long long rows = (long long)d.n_Om * d.n_T * pd.n_kap * pd.n_eta;
-    const long long B = (long long)d.n_ap * rows;
-    if (B > (1LL << 30)) return BSH_ERR_RANGE;
+    const long long rows = (long long)(h.orb.size() / 4);
+    const long long B = (long long)h.bap.size();
+    if (B > (1LL << 30) || B <= 0) return BSH_ERR_RANGE;
     pd.nOT = (int)rows;
     pd.B = (int)B;
     pd.n_patch = d.n_patch;
@@ -247,9 +281,8 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
         const double nt = (double)(h.ps[q + 1] - h.ps[q]) * (double)B * d.n_f0;
         if (nt >= 4294967295.0) return BSH_ERR_RANGE;
     }
-    double ap_max = 0.0;
-    for (double a : h.ap) ap_max = std::max(ap_max, a);
-    const double Om_max = c_bound(h);
+    double ap_max = 0.0, Om_max = 0.0;
+    binary_bounds(h, &ap_max, &Om_max);
     const int j_last = (pd.n_fb - 1) * pd.JB + JW;             // last f0 offset evaluated (+1 for a crossing)
     const double F_eval = d.F0 + j_last;
     const double phi = d.F0 - std::floor(d.F0);
@@ -278,8 +311,8 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
     if (wseg > 64) return BSH_ERR_RANGE;
     pd.Wseg = wseg;
     // a_p in fixed point
-    h.ap_q.resize(d.n_ap);
-    for (int k = 0; k < d.n_ap; ++k) h.ap_q[k] = (int32_t)std::llround(std::ldexp(h.ap[k], pd.fp.s_a));
+    h.bapq.resize(h.bap.size());
+    for (size_t k = 0; k < h.bap.size(); ++k) h.bapq[k] = (int32_t)std::llround(std::ldexp(h.bap[k], pd.fp.s_a));
     // patch of each sky point
     h.patch_of_s.assign(d.S, 0);
     for (int q = 0; q < d.n_patch; ++q)
@@ -374,13 +407,16 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
         ProbHost& h = p->P[q];
         h.d = problems[q];
         const bsh_problem& d = problems[q];
-        copy_grid(h, d);
+        expand_binaries(h, d);
         h.ps.assign(d.patch_start, d.patch_start + d.n_patch + 1);
         h.d.a_p = nullptr;
         h.d.Omega = nullptr;
         h.d.T_asc = nullptr;
         h.d.kappa = nullptr;
         h.d.eta = nullptr;
+        h.d.orbit = nullptr;
+        h.d.bank_orbit = nullptr;
+        h.d.bank_ap = nullptr;
         h.d.patch_start = nullptr;
     }
     // size the workspace for every tile shape the autotuner may pick
@@ -432,12 +468,17 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     // tile shapes
     p->ot_max = 1;
     p->wrows = 1;
+    // orbit rows spanned by one binary tile (CTA) and by one warp's 32 templates
     for (auto& h : p->P) {
-        const long long nOT = orbit_rows(h.d);
-        const int rows = (int)std::min(nOT, (long long)((p->threads + h.d.n_ap - 1) / h.d.n_ap + 1));
-        p->ot_max = std::max(p->ot_max, rows);
-        const int wr = (int)std::min(nOT, (long long)((32 + h.d.n_ap - 1) / h.d.n_ap + 1));
-        p->wrows = std::max(p->wrows, wr);
+        const int B = (int)h.brow.size();
+        for (int b0 = 0; b0 < B; b0 += p->threads) {
+            const int b1 = std::min(b0 + p->threads, B) - 1;
+            p->ot_max = std::max(p->ot_max, h.brow[b1] - h.brow[b0] + 1);
+            for (int w0 = b0; w0 <= b1; w0 += 32) {
+                const int w1 = std::min(w0 + 31, B - 1);
+                p->wrows = std::max(p->wrows, h.brow[w1] - h.brow[w0] + 1);
+            }
+        }
     }
     int region = 0;
     long long items = 0;
@@ -571,12 +612,10 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     p->off_probs = o; o = al(o + sizeof(ProbDev) * p->n);
     for (auto& h : p->P) {
         const ProbDev& pd = h.pd;
-        h.off_ap = o; o = al(o + sizeof(double) * pd.n_ap);
-        h.off_apq = o; o = al(o + sizeof(int32_t) * pd.n_ap);
-        h.off_Om = o; o = al(o + sizeof(double) * pd.n_Om);
-        h.off_Tasc = o; o = al(o + sizeof(double) * (size_t)pd.n_Om * pd.n_T);
-        h.off_kap = o; o = al(o + sizeof(double) * pd.n_kap);
-        h.off_eta = o; o = al(o + sizeof(double) * pd.n_eta);
+        h.off_orb = o; o = al(o + sizeof(double) * 4 * (size_t)pd.nOT);
+        h.off_brow = o; o = al(o + sizeof(int32_t) * (size_t)pd.B);
+        h.off_bap = o; o = al(o + sizeof(double) * (size_t)pd.B);
+        h.off_bapq = o; o = al(o + sizeof(int32_t) * (size_t)pd.B);
         h.off_ps = o; o = al(o + sizeof(int64_t) * (pd.n_patch + 1));
         h.off_pos = o; o = al(o + sizeof(int32_t) * pd.S);
         h.off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)pd.S * pd.Np);
@@ -700,12 +739,10 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
         pd.v = d.v;
         pd.t = d.t;
         pd.sky = d.sky;
-        pd.a_p = reinterpret_cast<const double*>(p->ws + h.off_ap);
-        pd.ap_q = reinterpret_cast<const int32_t*>(p->ws + h.off_apq);
-        pd.Om = reinterpret_cast<const double*>(p->ws + h.off_Om);
-        pd.Tasc = reinterpret_cast<const double*>(p->ws + h.off_Tasc);
-        pd.kap = h.kap.empty() ? nullptr : reinterpret_cast<const double*>(p->ws + h.off_kap);
-        pd.eta = h.eta.empty() ? nullptr : reinterpret_cast<const double*>(p->ws + h.off_eta);
+        pd.orb = reinterpret_cast<const double*>(p->ws + h.off_orb);
+        pd.brow = reinterpret_cast<const int32_t*>(p->ws + h.off_brow);
+        pd.bap = reinterpret_cast<const double*>(p->ws + h.off_bap);
+        pd.bapq = reinterpret_cast<const int32_t*>(p->ws + h.off_bapq);
         pd.patch_start = reinterpret_cast<const int64_t*>(p->ws + h.off_ps);
         pd.patch_of_s = reinterpret_cast<const int32_t*>(p->ws + h.off_pos);
         pd.vn_q = reinterpret_cast<int32_t*>(p->ws + h.off_vnq);
@@ -720,12 +757,10 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
         }
         hp[q] = pd;
         cudaError_t e = cudaSuccess;
-        e = e ? e : up(p->ws + h.off_ap, h.ap.data(), h.ap.size(), st);
-        e = e ? e : up(p->ws + h.off_apq, h.ap_q.data(), h.ap_q.size(), st);
-        e = e ? e : up(p->ws + h.off_Om, h.Om.data(), h.Om.size(), st);
-        e = e ? e : up(p->ws + h.off_Tasc, h.Tasc.data(), h.Tasc.size(), st);
-        if (!h.kap.empty()) e = e ? e : up(p->ws + h.off_kap, h.kap.data(), h.kap.size(), st);
-        if (!h.eta.empty()) e = e ? e : up(p->ws + h.off_eta, h.eta.data(), h.eta.size(), st);
+        e = e ? e : up(p->ws + h.off_orb, h.orb.data(), h.orb.size(), st);
+        e = e ? e : up(p->ws + h.off_brow, h.brow.data(), h.brow.size(), st);
+        e = e ? e : up(p->ws + h.off_bap, h.bap.data(), h.bap.size(), st);
+        e = e ? e : up(p->ws + h.off_bapq, h.bapq.data(), h.bapq.size(), st);
         e = e ? e : up(p->ws + h.off_ps, h.ps.data(), h.ps.size(), st);
         e = e ? e : up(p->ws + h.off_pos, h.patch_of_s.data(), h.patch_of_s.size(), st);
         if (e) return BSH_ERR_CUDA;
@@ -1005,15 +1040,22 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
                                        const uint32_t* row_bits, uint32_t* out, int32_t* path) {
     if (!hp || !query || count < 0 || !row_bits || !out || !path) return BSH_ERR_ARG;
     const bsh_problem& d = *hp;
-    if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || !d.v || !d.t || !d.sky || !d.a_p || !d.Omega ||
-        !d.T_asc || d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || d.n_f0 <= 0 || !finite_pos(d.v_max) ||
-        d.n_kappa < 0 || d.n_eta < 0 || (d.n_kappa > 0 && !d.kappa) || (d.n_eta > 0 && !d.eta))
+    if (d.N <= 0 || d.K <= 0 || d.W < (d.K + 31) / 32 || !d.v || !d.t || !d.sky || d.n_f0 <= 0 ||
+        !finite_pos(d.v_max))
         return BSH_ERR_ARG;
+    if (uses_bank(d)) {
+        if (d.n_bank <= 0 || !d.orbit || !d.bank_orbit || !d.bank_ap) return BSH_ERR_ARG;
+        for (int b = 0; b < d.n_bank; ++b)
+            if (d.bank_orbit[b] < 0 || d.bank_orbit[b] >= d.n_orbit) return BSH_ERR_ARG;
+    } else if (!d.a_p || !d.Omega || !d.T_asc || d.n_ap <= 0 || d.n_Om <= 0 || d.n_T <= 0 || d.n_kappa < 0 ||
+               d.n_eta < 0 || (d.n_kappa > 0 && !d.kappa) || (d.n_eta > 0 && !d.eta)) {
+        return BSH_ERR_ARG;
+    }
     bsh_plan tmp;
     tmp.threads = 256;
     ProbHost h;
     h.d = d;
-    copy_grid(h, d);
+    expand_binaries(h, d);
     const int64_t ps[2] = {0, d.S};
     h.ps.assign(ps, ps + 2);
     h.d.n_patch = 1;
@@ -1031,10 +1073,9 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
         volatile double t1 = v[0] * n[0], t2 = v[1] * n[1], t3 = v[2] * n[2];
         volatile double t12 = t1 + t2;
         const double vn = t12 + t3;
-        const int iap = b % d.n_ap, ot = b / d.n_ap;
-        const int ie = ot % pd.n_eta, ik = (ot / pd.n_eta) % pd.n_kap, r = ot / pd.n_eta / pd.n_kap;
-        const double Om = h.Om[r / d.n_T], Ta = h.Tasc[r];
-        const double kap = h.kap.empty() ? 0.0 : h.kap[ik], eta = h.eta.empty() ? 0.0 : h.eta[ie];
+        const double* orow = h.orb.data() + 4 * (size_t)h.brow[b];
+        const double Om = orow[0], Ta = orow[1], kap = orow[2], eta = orow[3];
+        const int apq = h.bapq[b];
         volatile double dt = d.t[i] - Ta;
         volatile double arg = Om * dt;
         volatile double g = std::cos(arg);
@@ -1049,13 +1090,13 @@ extern "C" int bsh_debug_track_windows(const bsh_problem* hp, const int32_t* que
         const int vq = (int)std::nearbyint(vn * sv);
         const int cq = (int)std::nearbyint(c * sc);
         const int F2a = (int)std::llround(2.0 * d.F0) + 2 * j0;
-        const int v0 = make_Z(F2a, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a, cq, fp));
-        const int v1 = make_Z(F2a + 62, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a + 62, cq, fp));
-        const int vr = make_Z(F2a + 30, vq, fp) - mulhi32(h.ap_q[iap], make_C(F2a + 30, cq, fp));
+        const int v0 = make_Z(F2a, vq, fp) - mulhi32(apq, make_C(F2a, cq, fp));
+        const int v1 = make_Z(F2a + 62, vq, fp) - mulhi32(apq, make_C(F2a + 62, cq, fp));
+        const int vr = make_Z(F2a + 30, vq, fp) - mulhi32(apq, make_C(F2a + 30, cq, fp));
         const uint32_t* row = row_bits + (size_t)e * d.W;
         const int pbase = pd.G0 + j0 - d.k_lo;
         const int pos = pbase + (vr >> fp.s_y);
-        const double ap = h.ap[iap];
+        const double ap = h.bap[b];
         auto exact_o = [&](int j) -> int {
             volatile double apc = ap * c;
             volatile double D = vn - apc;
@@ -1099,11 +1140,39 @@ unsigned char* static_scratch_ptr() {
     return ptrs[dev];
 }
 
-__global__ void static_ap_q(const ProbDev* probs) {
+// Compact grid arrays of a problem, staged in the static scratch.
+struct GridDev {
+    const double* a_p;     // [n_ap]
+    const double* Om;      // [n_Om]
+    const double* Ta;      // [n_Om][n_T]
+    const double* kap;     // [n_kap] or NULL
+    const double* eta;     // [n_eta] or NULL
+    int n_ap, n_T, n_kap, n_eta;
+};
+
+// Writes the orbit rows and per-template (row, a_p) of a grid in its template order.
+__global__ void static_expand(const ProbDev* probs, GridDev g) {
+    const ProbDev& P = probs[0];
+    const int nk = g.n_kap > 0 ? g.n_kap : 1, ne = g.n_eta > 0 ? g.n_eta : 1;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nOT; r += gridDim.x * blockDim.x) {
+        const int ie = r % ne, ik = (r / ne) % nk, t = r / ne / nk;   // t = iOm * n_T + iT
+        double* o = const_cast<double*>(P.orb) + 4 * (size_t)r;
+        o[0] = g.Om[t / g.n_T];
+        o[1] = g.Ta[t];
+        o[2] = g.kap ? g.kap[ik] : 0.0;
+        o[3] = g.eta ? g.eta[ie] : 0.0;
+    }
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.B; b += gridDim.x * blockDim.x) {
+        const_cast<int32_t*>(P.brow)[b] = b / g.n_ap;
+        const_cast<double*>(P.bap)[b] = g.a_p[b % g.n_ap];
+    }
+}
+
+__global__ void static_bapq(const ProbDev* probs) {
     const ProbDev& P = probs[0];
     const double sc = ldexp(1.0, P.fp.s_a);
-    for (int k = threadIdx.x; k < P.n_ap; k += blockDim.x)
-        const_cast<int32_t*>(P.ap_q)[k] = (int32_t)llrint(P.a_p[k] * sc);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.B; b += gridDim.x * blockDim.x)
+        const_cast<int32_t*>(P.bapq)[b] = (int32_t)llrint(P.bap[b] * sc);
 }
 
 // One warp per listed template: Eq. (26) along the track, as in the plan's power kernel.
@@ -1130,9 +1199,9 @@ __global__ void power_list_kernel(const ProbDev* probs, const int64_t* ids, int 
     const double F = P.F0 + (double)j;
     const int F2 = (int)llrint(2.0 * F);
     const int G = P.G0 + j;
-    const int iap = b % P.n_ap, ot = b / P.n_ap;
-    const int apq = P.ap_q[iap];
-    const double ap = P.a_p[iap];
+    const int ot = P.brow[b];
+    const int apq = P.bapq[b];
+    const double ap = P.bap[b];
     const int s_y = P.fp.s_y, M = P.fp.M;
     const int cell = 1 << s_y;
     const double* nv = P.sky + 3 * (size_t)s;
@@ -1191,13 +1260,10 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     pd.k_lo = d.k_lo;
     pd.n_f0 = d.n_f0;
     pd.S = d.S;
-    pd.n_ap = d.n_ap;
-    pd.n_Om = d.n_Om;
-    pd.n_T = d.n_T;
-    pd.n_kap = std::max(1, d.n_kappa);
-    pd.n_eta = std::max(1, d.n_eta);
-    const long long rows = orbit_rows(d);
-    const long long B = (long long)d.n_ap * rows;
+    const bool bank = uses_bank(d);
+    const int nk = std::max(1, d.n_kappa), ne = std::max(1, d.n_eta);
+    const long long rows = bank ? d.n_orbit : (long long)d.n_Om * d.n_T * nk * ne;
+    const long long B = binary_count(d);
     if (B > (1LL << 30) || (double)B * d.n_f0 * d.S > 9.0e18) return BSH_ERR_RANGE;
     pd.nOT = (int)rows;
     pd.B = (int)B;
@@ -1206,10 +1272,22 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     pd.G0 = (int)std::floor(d.F0);
     pd.p_th = std::exp(-d.rho_th);
     pd.v_max = d.v_max;
+    // largest a_p and |Omega g| bound, from the caller's arrays
     double ap_max = 0.0, Om_max = 0.0;
-    for (int k = 0; k < d.n_ap; ++k) ap_max = std::max(ap_max, d.a_p[k]);
-    for (int k = 0; k < d.n_Om; ++k) Om_max = std::max(Om_max, d.Omega[k]);
-    Om_max *= 1.0 + ecc_bound(d);
+    if (bank) {
+        for (int b = 0; b < d.n_bank; ++b) ap_max = std::max(ap_max, d.bank_ap[b]);
+        for (int r = 0; r < d.n_orbit; ++r) {
+            const double* o = d.orbit + 4 * (size_t)r;
+            Om_max = std::max(Om_max, o[0] * (1.0 + std::fabs(o[2]) + std::fabs(o[3])));
+        }
+    } else {
+        double km = 0.0, em = 0.0;
+        for (int k = 0; k < d.n_ap; ++k) ap_max = std::max(ap_max, d.a_p[k]);
+        for (int k = 0; k < d.n_Om; ++k) Om_max = std::max(Om_max, d.Omega[k]);
+        for (int k = 0; k < d.n_kappa; ++k) km = std::max(km, std::fabs(d.kappa[k]));
+        for (int k = 0; k < d.n_eta; ++k) em = std::max(em, std::fabs(d.eta[k]));
+        Om_max *= 1.0 + km + em;
+    }
     // the same fixed-point scales as a plan of this problem
     const int nb = (d.n_f0 + JW - 1) / JW;
     const int JB = (d.n_f0 + nb - 1) / nb;
@@ -1225,16 +1303,22 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     // scratch layout inside the static array
     size_t o = 0;
     const size_t off_pd = o; o = al(o + sizeof(ProbDev));
-    const size_t off_ap = o; o = al(o + sizeof(double) * d.n_ap);
-    const size_t off_apq = o; o = al(o + sizeof(int32_t) * d.n_ap);
-    const size_t off_Om = o; o = al(o + sizeof(double) * d.n_Om);
-    const size_t off_Ta = o; o = al(o + sizeof(double) * (size_t)d.n_Om * d.n_T);
-    const size_t off_kap = o; o = al(o + sizeof(double) * pd.n_kap);
-    const size_t off_eta = o; o = al(o + sizeof(double) * pd.n_eta);
+    const size_t off_orb = o; o = al(o + sizeof(double) * 4 * (size_t)rows);
+    const size_t off_brow = o; o = al(o + sizeof(int32_t) * (size_t)B);
+    const size_t off_bap = o; o = al(o + sizeof(double) * (size_t)B);
+    const size_t off_bapq = o; o = al(o + sizeof(int32_t) * (size_t)B);
+    size_t off_gap = 0, off_gOm = 0, off_gTa = 0, off_gk = 0, off_ge = 0;
+    if (!bank) {
+        off_gap = o; o = al(o + sizeof(double) * d.n_ap);
+        off_gOm = o; o = al(o + sizeof(double) * d.n_Om);
+        off_gTa = o; o = al(o + sizeof(double) * (size_t)d.n_Om * d.n_T);
+        off_gk = o; o = al(o + sizeof(double) * nk);
+        off_ge = o; o = al(o + sizeof(double) * ne);
+    }
     const size_t off_vnq = o; o = al(o + sizeof(int32_t) * (size_t)d.S * pd.Np);
     const size_t off_w = o; o = al(o + sizeof(float) * (size_t)d.S * pd.Np);
-    const size_t off_cq = o; o = al(o + sizeof(int32_t) * (size_t)pd.nOT * pd.Np);
-    const size_t off_c64 = o; o = al(o + sizeof(double) * (size_t)pd.nOT * pd.Np);
+    const size_t off_cq = o; o = al(o + sizeof(int32_t) * (size_t)rows * pd.Np);
+    const size_t off_c64 = o; o = al(o + sizeof(double) * (size_t)rows * pd.Np);
     if (o > (size_t)BSH_STATIC_SCRATCH_BYTES) return BSH_ERR_WORKSPACE;
     unsigned char* base = static_scratch_ptr();
     unsigned* sp = status_ptr();
@@ -1247,28 +1331,46 @@ extern "C" int bsh_power_sum_static(const bsh_problem* problem, const int64_t* t
     pd.v = d.v;
     pd.t = d.t;
     pd.sky = d.sky;
-    pd.a_p = reinterpret_cast<const double*>(base + off_ap);
-    pd.ap_q = reinterpret_cast<const int32_t*>(base + off_apq);
-    pd.Om = reinterpret_cast<const double*>(base + off_Om);
-    pd.Tasc = reinterpret_cast<const double*>(base + off_Ta);
-    pd.kap = d.n_kappa > 0 ? reinterpret_cast<const double*>(base + off_kap) : nullptr;
-    pd.eta = d.n_eta > 0 ? reinterpret_cast<const double*>(base + off_eta) : nullptr;
+    pd.orb = reinterpret_cast<const double*>(base + off_orb);
+    pd.brow = reinterpret_cast<const int32_t*>(base + off_brow);
+    pd.bap = reinterpret_cast<const double*>(base + off_bap);
+    pd.bapq = reinterpret_cast<const int32_t*>(base + off_bapq);
     pd.vn_q = reinterpret_cast<int32_t*>(base + off_vnq);
     pd.w32 = reinterpret_cast<float*>(base + off_w);
     pd.c_q = reinterpret_cast<int32_t*>(base + off_cq);
     pd.c64 = reinterpret_cast<double*>(base + off_c64);
     cudaError_t e = cudaMemcpyAsync(base + off_pd, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
-    e = e ? e : cudaMemcpyAsync(base + off_ap, d.a_p, sizeof(double) * d.n_ap, cudaMemcpyHostToDevice, st);
-    e = e ? e : cudaMemcpyAsync(base + off_Om, d.Omega, sizeof(double) * d.n_Om, cudaMemcpyHostToDevice, st);
-    e = e ? e : cudaMemcpyAsync(base + off_Ta, d.T_asc, sizeof(double) * (size_t)d.n_Om * d.n_T,
-                                cudaMemcpyHostToDevice, st);
-    if (d.n_kappa > 0)
-        e = e ? e : cudaMemcpyAsync(base + off_kap, d.kappa, sizeof(double) * d.n_kappa, cudaMemcpyHostToDevice, st);
-    if (d.n_eta > 0)
-        e = e ? e : cudaMemcpyAsync(base + off_eta, d.eta, sizeof(double) * d.n_eta, cudaMemcpyHostToDevice, st);
+    GridDev g{};
+    if (bank) {
+        e = e ? e : cudaMemcpyAsync(base + off_orb, d.orbit, sizeof(double) * 4 * (size_t)rows,
+                                    cudaMemcpyHostToDevice, st);
+        e = e ? e : cudaMemcpyAsync(base + off_brow, d.bank_orbit, sizeof(int32_t) * (size_t)B,
+                                    cudaMemcpyHostToDevice, st);
+        e = e ? e : cudaMemcpyAsync(base + off_bap, d.bank_ap, sizeof(double) * (size_t)B, cudaMemcpyHostToDevice,
+                                    st);
+    } else {
+        e = e ? e : cudaMemcpyAsync(base + off_gap, d.a_p, sizeof(double) * d.n_ap, cudaMemcpyHostToDevice, st);
+        e = e ? e : cudaMemcpyAsync(base + off_gOm, d.Omega, sizeof(double) * d.n_Om, cudaMemcpyHostToDevice, st);
+        e = e ? e : cudaMemcpyAsync(base + off_gTa, d.T_asc, sizeof(double) * (size_t)d.n_Om * d.n_T,
+                                    cudaMemcpyHostToDevice, st);
+        if (d.n_kappa > 0)
+            e = e ? e : cudaMemcpyAsync(base + off_gk, d.kappa, sizeof(double) * d.n_kappa, cudaMemcpyHostToDevice, st);
+        if (d.n_eta > 0)
+            e = e ? e : cudaMemcpyAsync(base + off_ge, d.eta, sizeof(double) * d.n_eta, cudaMemcpyHostToDevice, st);
+        g.a_p = reinterpret_cast<const double*>(base + off_gap);
+        g.Om = reinterpret_cast<const double*>(base + off_gOm);
+        g.Ta = reinterpret_cast<const double*>(base + off_gTa);
+        g.kap = d.n_kappa > 0 ? reinterpret_cast<const double*>(base + off_gk) : nullptr;
+        g.eta = d.n_eta > 0 ? reinterpret_cast<const double*>(base + off_ge) : nullptr;
+        g.n_ap = d.n_ap;
+        g.n_T = d.n_T;
+        g.n_kap = d.n_kappa;
+        g.n_eta = d.n_eta;
+    }
     if (e) return BSH_ERR_CUDA;
     const ProbDev* dpd = reinterpret_cast<const ProbDev*>(base + off_pd);
-    static_ap_q<<<1, 256, 0, st>>>(dpd);
+    if (!bank) static_expand<<<64, 256, 0, st>>>(dpd, g);
+    static_bapq<<<64, 256, 0, st>>>(dpd);
     launch_tables(pd, dpd, BSH_MODE_BATCHED, sp, st);
     const int warps = 8;
     power_list_kernel<<<(n + warps - 1) / warps, warps * 32, 0, st>>>(dpd, template_ids, n, power, s_p, sp);

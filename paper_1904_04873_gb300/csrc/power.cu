@@ -29,9 +29,9 @@ __global__ void __launch_bounds__(PW * 32) power_kernel(const PowerArgs a) {
     const double F = P.F0 + (double)j;
     const int F2 = (int)llrint(2.0 * F);
     const int G = P.G0 + j;
-    const int iap = b % P.n_ap, ot = b / P.n_ap;
-    const int apq = P.ap_q[iap];
-    const double ap = P.a_p[iap];
+    const int ot = P.brow[b];
+    const int apq = P.bapq[b];
+    const double ap = P.bap[b];
     const int s_y = P.fp.s_y, M = P.fp.M;
     const int cell = 1 << s_y;
     const bool plain = P.w64 != nullptr && P.w32 == nullptr;

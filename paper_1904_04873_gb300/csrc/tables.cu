@@ -4,7 +4,7 @@
 //   c64[ot][i]  = Omega g,  g = (cos(phi) + kappa cos(2 phi)) + eta sin(2 phi),
 //                 phi = Omega (t_i - t_asc)  (Eq. (14); g = cos(phi) when kappa = eta = 0)
 //   c_q = round(c64 * 2^s_c)
-// Orbit row ot = ((iOm * n_T + iT) * n_kap + ik) * n_eta + ie.
+// for every orbit row ot = (Omega, t_asc, kappa, eta).
 //   w32 / w64   = the problem's weights widened exactly (fp16/bf16/fp32 -> fp32, any -> fp64)
 // The products are rounded individually (no fused multiply-add) so that the
 // FP64 values equal those of a plain sequential evaluation of the formula.
@@ -63,14 +63,8 @@ __global__ void binary_tables(const ProbDev* __restrict__ probs, int q, unsigned
         double c = 0.0;
         int32_t cq = 0;
         if (i < P.N) {
-            const int ie = ot % P.n_eta;
-            const int r1 = ot / P.n_eta;
-            const int ik = r1 % P.n_kap;
-            const int r = r1 / P.n_kap;          // iOm * n_T + iT
-            const double Om = P.Om[r / P.n_T];
-            const double Ta = P.Tasc[r];
-            const double kap = P.kap ? P.kap[ik] : 0.0;
-            const double eta = P.eta ? P.eta[ie] : 0.0;
+            const double* o = P.orb + 4 * (size_t)ot;
+            const double Om = o[0], Ta = o[1], kap = o[2], eta = o[3];
             const double arg = __dmul_rn(Om, __dsub_rn(P.t[i], Ta));
             double g = cos(arg);
             if (kap != 0.0 || eta != 0.0) {

@@ -168,6 +168,11 @@ class Problem:
     top_k: int = 1000
     kappa: Optional[np.ndarray] = None   # [n_kap] e cos(omega) (Eq. (14)); None: circular orbits
     eta: Optional[np.ndarray] = None     # [n_eta] e sin(omega)
+    # explicit binary bank (replaces the grid above when set): orbit rows [R][4]
+    # (Omega, t_asc, kappa, eta) and, per binary template, its row and a_p
+    orbit: Optional[np.ndarray] = None
+    bank_orbit: Optional[np.ndarray] = None
+    bank_ap: Optional[np.ndarray] = None
 
     @property
     def N(self) -> int:
@@ -179,6 +184,8 @@ class Problem:
 
     @property
     def B(self) -> int:
+        if self.orbit is not None:
+            return int(np.size(self.bank_ap))
         nk = 1 if self.kappa is None else int(np.size(self.kappa))
         ne = 1 if self.eta is None else int(np.size(self.eta))
         return int(self.a_p.size * self.T_asc.size * nk * ne)
@@ -274,6 +281,25 @@ def make_problem(name: str, *, n_per_det: int, dets: List[str], T_sft: float, sp
                    eta=None if eta is None else np.asarray(eta, dtype=np.float64))
 
 
+def grid_as_bank(pr: Problem) -> Problem:
+    """The same problem with its binary grid written out as an explicit bank, in the
+    grid's template order b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap."""
+    kap = np.zeros(1) if pr.kappa is None else np.asarray(pr.kappa, dtype=np.float64)
+    eta = np.zeros(1) if pr.eta is None else np.asarray(pr.eta, dtype=np.float64)
+    n_T = pr.T_asc.shape[1]
+    rows = []
+    for iOm in range(pr.Omega.size):
+        for iT in range(n_T):
+            for k in kap:
+                for e in eta:
+                    rows.append((pr.Omega[iOm], pr.T_asc[iOm, iT], k, e))
+    orbit = np.array(rows, dtype=np.float64)
+    n_ap = pr.a_p.size
+    bank_orbit = np.repeat(np.arange(orbit.shape[0], dtype=np.int32), n_ap)
+    bank_ap = np.tile(np.asarray(pr.a_p, dtype=np.float64), orbit.shape[0])
+    return dataclasses.replace(pr, orbit=orbit, bank_orbit=bank_orbit, bank_ap=bank_ap)
+
+
 def tiny(seed: int = SEED_NOISE) -> Problem:
     """Plain method, tiny: 1 detector, 200 SFTs of 900 s over 30 days, rho ~ Exp(1),
     band 100.0-100.1 Hz, 8 sky x 4 a_p x 4 Omega x 4 t_asc x 90 f0."""
@@ -325,6 +351,39 @@ def eccentric(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 16, n_P: int
                         P_days=np.linspace(15.0, 45.0, n_P), n_T=n_T, power_kind="gauss", seed=seed,
                         top_k=top_k, kappa=np.linspace(-e_max, e_max, n_kap),
                         eta=np.linspace(-e_max, e_max, n_eta))
+
+
+def metric(n_sky: int = 2000, n_per_det: int = 2000, ap_range=(3.0, 13.0), P_days=(10.0, 20.0),
+           seed: int = SEED_NOISE, patch_size: int = 50, top_k: int = 1000, sky: Optional[np.ndarray] = None) -> Problem:
+    """Search over a binary template bank: the mid construction (2 x 2000 SFTs over 1 yr,
+    0.1 Hz at 200 Hz, patches of 50) over the BS3 ranges of the paper's simulations
+    (Sec. VI.A: a_p 3-13 ls, P 10-20 d).  The grid fields hold only the range's corners
+    (they size the loaded band); attach the bank with attach_bank()."""
+    if sky is None:
+        sky = fibonacci_sky(n_sky)
+    return make_problem("metric", n_per_det=n_per_det, dets=["H1", "L1"], T_sft=900.0, span=YEAR_SID,
+                        random_times=True, f_lo=200.0, n_f0=90, half_bin=False, sky=sky,
+                        patch_size=patch_size, a_p=np.array(ap_range, dtype=np.float64),
+                        P_days=np.array([P_days[1], P_days[0]], dtype=np.float64), n_T=1, power_kind="gauss",
+                        seed=seed, top_k=top_k)
+
+
+def metric_spec(pr: Problem, m: float = 6.4, ap_block: float = 2.0) -> dict:
+    """Bank parameters for a metric() problem: spacings at the band's top frequency,
+    T_obs the span of the SFTs, t_asc around the mid-time (t = 0), equal mismatch
+    parameters m for a_p, Omega and t_asc."""
+    f_top = (pr.F0 + pr.n_f0 - 1) / pr.T_sft
+    T_obs = float(pr.t.max() - pr.t.min()) + pr.T_sft
+    return dict(f=f_top, T_c=pr.T_sft, T_obs=T_obs, t_mid=0.0, ap_min=float(pr.a_p.min()),
+                ap_max=float(pr.a_p.max()), P_min=2.0 * math.pi / float(pr.Omega.max()),
+                P_max=2.0 * math.pi / float(pr.Omega.min()), m_a=m, m_Om=m, m_t=m, ap_block=ap_block)
+
+
+def attach_bank(pr: Problem, orbit, bank_orbit, bank_ap) -> Problem:
+    """The problem searching the given explicit binary bank."""
+    return dataclasses.replace(pr, orbit=np.asarray(orbit, dtype=np.float64).reshape(-1, 4),
+                               bank_orbit=np.asarray(bank_orbit, dtype=np.int32),
+                               bank_ap=np.asarray(bank_ap, dtype=np.float64))
 
 
 def precision_stress(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,

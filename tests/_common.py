@@ -23,7 +23,8 @@ def oracle_inputs(pr, dtype="f64"):
 def oracle_problem(pr, bits, w, rho=None):
     return oracle.OracleProblem(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky,
                                 a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K,
-                                rho=rho, rho_th=pr.rho_th, kappa=pr.kappa, eta=pr.eta)
+                                rho=rho, rho_th=pr.rho_th, kappa=pr.kappa, eta=pr.eta, orbit=pr.orbit,
+                                bank_orbit=pr.bank_orbit, bank_ap=pr.bank_ap)
 
 
 def pack_bits(on, W):
@@ -37,7 +38,10 @@ def pack_bits(on, W):
 
 def orbit_of(pr, b):
     """(a_p, Omega, t_asc, kappa, eta) of binary index b:
-    b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap."""
+    b = (((iOm * n_T + iT) * n_kap + ik) * n_eta + ie) * n_ap + iap, or the bank's entry b."""
+    if pr.orbit is not None:
+        Om, Ta, kap, eta = pr.orbit[pr.bank_orbit[b]]
+        return pr.bank_ap[b], Om, Ta, float(kap), float(eta)
     nk = 1 if pr.kappa is None else pr.kappa.size
     ne = 1 if pr.eta is None else pr.eta.size
     iap = b % pr.a_p.size
@@ -55,7 +59,7 @@ def orbit_of(pr, b):
 
 def template_of(pr, b):
     """(a_p, Omega, t_asc) of binary index b of a circular-orbit problem."""
-    assert pr.kappa is None and pr.eta is None
+    assert pr.kappa is None and pr.eta is None and pr.orbit is None
     return orbit_of(pr, b)[:3]
 
 

@@ -73,6 +73,15 @@ def test_static_power_sum_eccentric_grid():
     _check(dp, ref)
 
 
+def test_static_power_sum_explicit_bank():
+    # an explicit (metric) bank is staged in the static array as given
+    from test_gpu_bank import metric_slice
+    pr = metric_slice(rows=(0, 300), top_k=20)
+    dp, _, _ = device_problem(pr, "f16")
+    ref = _reference(dp, 20)
+    _check(dp, ref)
+
+
 def test_static_power_sum_rejects_oversized_problem():
     pr = small_mid(n_sky=2, n_per_det=64, n_ap=2, n_P=2, n_T=2, patch_size=2, top_k=5)
     dp, _, _ = device_problem(pr, "f16")
