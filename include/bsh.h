@@ -318,6 +318,74 @@ int bsh_debug_track_windows(const bsh_problem* host_problem, const int32_t* quer
                             int count, const uint32_t* row_bits, uint32_t* out, int32_t* path);
 
 /* ------------------------------------------------------------------------ */
+/* (vi) Post-processing, Sec. V.E: candidate parameters, the distance of      */
+/* Eq. (44), coincidences between two lists (option A), clustering, the       */
+/* option-B cut, significance-weighted centroids and each band's most         */
+/* significant cluster.                                                       */
+/*                                                                          */
+/* Parameters of a candidate: (f in Hz, x, y, a_p, Omega, t_asc), x and y the */
+/* sky direction in ecliptic Cartesian coordinates projected on the ecliptic  */
+/* plane (x = n_x, y = cos(obliquity) n_y + sin(obliquity) n_z).  Distance:   */
+/*   d^2 = sum over the six parameters of (difference / resolution)^2,        */
+/* each resolution the mean of its values at the two candidates: delta f =   */
+/* 1/T_c; delta theta = 1/(v_over_c T_c f P_F) for x and y; delta a_p, delta  */
+/* Omega, delta t_asc of Eq. (30)-(32).  Thresholds are strict (d < d_cluster,*/
+/* d < d_coinc); the cut keeps d <= d_cut.  Centroid weights are max(sig, 0), */
+/* the plain mean where they sum to 0.  FP64 throughout, each operation       */
+/* rounded separately.                                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct bsh_post_params {
+    double T_c;                /* coherence time (s): f = F / T_c, delta f = 1 / T_c */
+    double T_obs;              /* observation time (s), Eq. (31) */
+    double v_over_c;           /* detector speed / c in delta theta (Sec. V.B) */
+    double P_F;                /* pixel factor of delta theta */
+    double m_a, m_Om, m_t;     /* mismatch parameters of Eq. (30)-(32) */
+    double obliquity;          /* rad, equatorial -> ecliptic rotation about x */
+    double d_cluster;          /* clustering threshold (bins; sqrt(14) in Sec. VI) */
+    double d_cut;              /* option-B cut around each cluster's top member (bins); <= 0: none */
+    double d_coinc;            /* coincidence threshold (bins; 3 in Sec. VI) */
+} bsh_post_params;
+
+/* Parameters of problem `problem`'s candidates: region r = first_region + p  */
+/* (patch p), rank e < per_region give row n = p * per_region + e of params   */
+/* [n][6] and sig [n] (s_H with stat 0, s_P with stat 1) as doubles; valid [n] */
+/* = e < n_cands[r].  cands [regions][per_region], n_cands [regions]: the     */
+/* lists of bsh_toplist (per_region = top_k) or bsh_power_sum's final lists   */
+/* (per_region = n_cf).  All DEVICE.  Capturable.                            */
+int bsh_cand_params(bsh_plan* plan, int problem, const bsh_cand* cands, const int32_t* n_cands, int per_region,
+                    int stat, const bsh_post_params* pp, double* params, double* sig, int32_t* valid,
+                    bsh_stream stream);
+
+/* Workspace bytes of bsh_cluster for n candidates. */
+size_t bsh_cluster_workspace(int n);
+
+/* Clusters one band's n <= 2^20 candidates (DEVICE arrays): label [n] = the  */
+/* smallest index of the candidate's connected component (edges between valid */
+/* candidates with d < d_cluster), -1 where valid[i] = 0; keep [n] = 1 for    */
+/* members within d_cut of their cluster's top member (largest sig, then the  */
+/* smallest index); centroid [n][6] and csig [n] at each root's row (label[i] */
+/* == i): the weighted mean and the summed sig of the kept members (NaN and 0 */
+/* at the other rows); best [1] = the root with the largest csig (ties: the   */
+/* smallest root), -1 if there is none.  work: bsh_cluster_workspace(n)       */
+/* bytes of DEVICE memory.  Capturable.                                      */
+int bsh_cluster(const double* params, const double* sig, const int32_t* valid, int n, const bsh_post_params* pp,
+                void* work, size_t work_bytes, int32_t* label, int32_t* keep, double* centroid, double* csig,
+                int32_t* best, bsh_stream stream);
+
+/* Workspace bytes of bsh_coincidences. */
+size_t bsh_coincidence_workspace(int na, int nb);
+
+/* Option A: every pair (i of list A, j of list B, both valid) with d <       */
+/* d_coinc, in an unspecified order: pairs [cap][2] = (i, j), centroid        */
+/* [cap][6] and sig [cap] = sa[i] + sb[j]; n_pairs [1] = the number of pairs  */
+/* found (entries past cap are not written).  DEVICE arrays; na, nb <= 2^20.  */
+/* Capturable.                                                                */
+int bsh_coincidences(const double* pa, const double* sa, const int32_t* va, int na, const double* pb,
+                     const double* sb, const int32_t* vb, int nb, const bsh_post_params* pp, void* work,
+                     size_t work_bytes, int32_t* pairs, double* centroid, double* sig, int cap, int32_t* n_pairs,
+                     bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Binary template bank, Sec. V.B, Eq. (30)-(32).  HOST only, no CUDA call.   */
 /*                                                                          */
 /* bsh_binary_resolution: the spacings at (f, a_p, Omega) for the mismatch   */

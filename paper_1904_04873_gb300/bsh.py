@@ -130,9 +130,36 @@ _SIGS = {
     "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_binary_resolution": (ctypes.c_int, [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3),
+    "bsh_cand_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_cluster_workspace": (ctypes.c_size_t, [ctypes.c_int]),
+    "bsh_cluster": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "bsh_coincidence_workspace": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "bsh_coincidences": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "bsh_template_bank": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
+
+
+class PostParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("T_c", "T_obs", "v_over_c", "P_F", "m_a", "m_Om", "m_t", "obliquity",
+                                               "d_cluster", "d_cut", "d_coinc")]
+
+
+def post_params(**kw) -> PostParams:
+    """bsh_post_params with the values of Sec. VI as defaults (clustering window sqrt(14)
+    bins, coincidence window 3 bins, v/c = 1e-4, pixel factor 2, no cut)."""
+    d = dict(T_c=900.0, T_obs=3.15e7, v_over_c=1e-4, P_F=2.0, m_a=1.0, m_Om=1.0, m_t=1.0,
+             obliquity=0.40909280422232897, d_cluster=14.0 ** 0.5, d_cut=0.0, d_coinc=3.0)
+    d.update(kw)
+    return PostParams(**{k: float(v) for k, v in d.items()})
 
 
 class BankSpec(ctypes.Structure):
@@ -439,3 +466,51 @@ def template_bank(**spec):
     _check(lib().bsh_template_bank(ctypes.byref(sp), ctypes.byref(nr), orbit.ctypes.data, orbit.shape[0],
                                    ctypes.byref(nb), bo.ctypes.data, ba.ctypes.data, bo.size), "bsh_template_bank")
     return orbit, bo, ba
+
+
+def cand_params(plan: "Plan", problem: int, cands, n_cands, stat: int, pp: PostParams, stream=None):
+    """bsh_cand_params: (params [n][6], sig [n], valid [n]) device tensors for one problem's lists."""
+    import torch
+    per_region = cands.shape[1]
+    n_patch = len(plan.problems[problem].pr.patch_start) - 1
+    n = n_patch * per_region
+    dev = cands.device
+    params = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    sig = torch.empty(n, dtype=torch.float64, device=dev)
+    valid = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib().bsh_cand_params(plan.h, problem, _ptr(cands), _ptr(n_cands), per_region, stat, ctypes.byref(pp),
+                                 _ptr(params), _ptr(sig), _ptr(valid), _stream(stream)), "bsh_cand_params")
+    return params, sig, valid
+
+
+def cluster(params, sig, valid, pp: PostParams, stream=None):
+    """bsh_cluster: (label, keep, centroid, csig, best) device tensors."""
+    import torch
+    n = params.shape[0]
+    dev = params.device
+    work = torch.empty(max(1, lib().bsh_cluster_workspace(n)), dtype=torch.uint8, device=dev)
+    label = torch.empty(n, dtype=torch.int32, device=dev)
+    keep = torch.empty(n, dtype=torch.int32, device=dev)
+    centroid = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    csig = torch.empty(n, dtype=torch.float64, device=dev)
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib().bsh_cluster(_ptr(params), _ptr(sig), _ptr(valid), n, ctypes.byref(pp), _ptr(work), work.numel(),
+                             _ptr(label), _ptr(keep), _ptr(centroid), _ptr(csig), _ptr(best), _stream(stream)),
+           "bsh_cluster")
+    return label, keep, centroid, csig, best
+
+
+def coincidences(pa, sa, va, pb, sb, vb, pp: PostParams, cap: int, stream=None):
+    """bsh_coincidences: (pairs [cap][2], centroid [cap][6], sig [cap], n_pairs [1]) device tensors."""
+    import torch
+    dev = pa.device
+    na, nb = pa.shape[0], pb.shape[0]
+    work = torch.empty(max(1, lib().bsh_coincidence_workspace(na, nb)), dtype=torch.uint8, device=dev)
+    pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    cen = torch.empty((cap, 6), dtype=torch.float64, device=dev)
+    sig = torch.empty(cap, dtype=torch.float64, device=dev)
+    n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib().bsh_coincidences(_ptr(pa), _ptr(sa), _ptr(va), na, _ptr(pb), _ptr(sb), _ptr(vb), nb,
+                                  ctypes.byref(pp), _ptr(work), work.numel(), _ptr(pairs), _ptr(cen), _ptr(sig),
+                                  cap, _ptr(n_pairs), _stream(stream)), "bsh_coincidences")
+    return pairs, cen, sig, n_pairs

@@ -326,6 +326,9 @@ struct TmapSet {
 };
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st);
+int launch_cand_params(const ProbDev* dprob, int first_region, int n_patch, int per_region, const bsh_cand* cands,
+                       const int32_t* n_cands, int stat, const bsh_post_params* pp, double* params, double* sig,
+                       int32_t* valid, cudaStream_t st);
 void launch_tables(const ProbDev& hp, const ProbDev* dprob, int mode, unsigned* status, cudaStream_t st);
 void launch_peakgram(const float* power, int N, int K, int window, double rho_th, float* rho,
                      uint32_t* bits, int W, cudaStream_t st);

@@ -932,6 +932,19 @@ int bsh_track_bins(bsh_plan* p, int problem, const int64_t* ids, int n, int32_t*
     return cuda_fail(cudaGetLastError());
 }
 
+int bsh_cand_params(bsh_plan* p, int problem, const bsh_cand* cands, const int32_t* n_cands, int per_region,
+                    int stat, const bsh_post_params* pp, double* params, double* sig, int32_t* valid,
+                    bsh_stream stream) {
+    if (!p || !p->bound) return BSH_ERR_STATE;
+    if (problem < 0 || problem >= p->n || !cands || !n_cands || per_region <= 0 || (stat != 0 && stat != 1) ||
+        !params || !sig || !valid)
+        return BSH_ERR_ARG;
+    const ProbHost& h = p->P[problem];
+    const ProbDev* dprob = reinterpret_cast<const ProbDev*>(p->ws + p->off_probs) + problem;
+    return launch_cand_params(dprob, h.pd.region_base, h.pd.n_patch, per_region, cands, n_cands, stat, pp, params,
+                              sig, valid, (cudaStream_t)stream);
+}
+
 int bsh_count_dense(bsh_plan* p, int32_t* const* n_unw, float* const* n_w, bsh_stream stream) {
     if (!p || !p->bound) return BSH_ERR_STATE;
     if (!n_unw || !n_w) return BSH_ERR_ARG;
