@@ -4,6 +4,7 @@
     python -m paper_1904_04873_gb300.experiments batching [--patches P] [--steps K]
     python -m paper_1904_04873_gb300.experiments full [--sky N] [--injections M]
     python -m paper_1904_04873_gb300.experiments lut [--sky N]
+    python -m paper_1904_04873_gb300.experiments metric [--sky N] [--injections M] [--mismatch m]
 
 precision  Half-bin f0 grid with forced exact ties: the fixed-point track of the
            batched kernels against the exact FP64 bins for every term of a sky
@@ -16,6 +17,12 @@ full       2 x 4000 SFTs, 10 Hz at 300 Hz, patches of 169 sky points, 8^3 binary
            templates, top-10000, stage-2 power sum; seeded injections placed on
            their exact tracks; recovery = a toplist entry within one grid step of
            the injection in every parameter.
+metric     A search over a binary template bank with the spacings of Eq. (30)-(32)
+           (the BS3 ranges of Sec. VI.A: a_p 3-13 ls, P 10-20 d) with seeded
+           injections, stage 2, and the post-processing of Sec. V.E on the GPU:
+           clusters of each band's final lists, and recovery = a kept cluster's
+           centroid within 13 bins (Eq. (44)) of the injection, the criterion of
+           Sec. VI.A.
 lut        Exact track against the look-up-table approximation of Sec. IV.B
            (BSH_MODE_LUT) on the mid workload and on a fast-binary variant
            (P = 1.5-3 d, a_p = 10-60 ls): number-count throughput of both, the
@@ -207,6 +214,116 @@ def full(n_sky: int = 100048, n_inj: int = 100, depth_amp: float = 0.5, top_k: i
             "efficiency_error": math.sqrt(E * (1 - E) / n_inj)}
 
 
+def metric(n_sky: int = 2000, n_inj: int = 20, depth_amp: float = 0.5, m: float = 6.4, ap_block: float = 2.0,
+           n_cf: int = 100, seed: int = synth.SEED_INJ) -> dict:
+    """Bank search with injections, stage 2 and GPU post-processing."""
+    import torch
+    pr = synth.metric(n_sky=n_sky)
+    spec = synth.metric_spec(pr, m=m, ap_block=ap_block)
+    pr = synth.attach_bank(pr, *bsh.template_bank(**spec))
+    rng = np.random.default_rng(seed)
+    inj = []
+    for _ in range(n_inj):
+        s = int(rng.integers(pr.S))
+        b = int(rng.integers(pr.B))
+        j = int(rng.integers(2, pr.n_f0 - 2))
+        inj.append((s * pr.B + b) * pr.n_f0 + j)
+    dp = bsh.DeviceProblem(pr, w_dtype="f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    ids = torch.as_tensor(np.array(inj, dtype=np.int64), device="cuda")
+    bins = plan.track_bins(ids).cpu().numpy()
+    power = pr.power.copy()
+    srng = np.random.default_rng(seed + 1)
+    for q in range(n_inj):
+        cols = bins[q] - pr.k_lo
+        ph = srng.uniform(0, 2 * math.pi)
+        amp = depth_amp * np.sqrt(pr.Sn)
+        re = srng.standard_normal(pr.N) * np.sqrt(0.5 * pr.Sn) + amp * math.cos(ph)
+        im = srng.standard_normal(pr.N) * np.sqrt(0.5 * pr.Sn) + amp * math.sin(ph)
+        power[np.arange(pr.N), cols] = (re * re + im * im).astype(np.float32)
+    dp.power.copy_(torch.as_tensor(power))
+    dp.prepare()
+    tile = plan.autotune()
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    plan.number_count()
+    e1.record()
+    cands, n = plan.toplist()
+    final, nf = plan.power_sum(n_cf)
+    torch.cuda.synchronize()
+    t_count = e0.elapsed_time(e1) / 1e3
+    # post-processing of the band's final lists (s_P), on the GPU
+    pp = bsh.post_params(T_c=pr.T_sft, T_obs=spec["T_obs"], m_a=m, m_Om=m, m_t=m, d_cut=math.sqrt(14.0))
+    c0, c1 = _events()
+    c0.record()
+    params, sig, valid = bsh.cand_params(plan, 0, final, nf, 1, pp)
+    label, keep, cen, csig, best = bsh.cluster(params, sig, valid, pp)
+    c1.record()
+    torch.cuda.synchronize()
+    assert bsh.sync_status() == bsh.OK
+    t_post = c0.elapsed_time(c1) / 1e3
+    lab = label.cpu().numpy()
+    roots = np.nonzero(lab == np.arange(lab.size))[0]
+    # recovery: a cluster centroid within 13 bins of the injection (GPU coincidences of the
+    # injections' true parameters against the centroids)
+    ones = torch.ones(n_inj, dtype=torch.int32, device="cuda")
+    true_p, _, _ = bsh.cand_params(plan, 0, *_id_lists(plan, pr, inj), 0, pp)
+    tp = true_p.cpu().numpy()
+    truth = torch.as_tensor(np.stack([tp[q] for q in _rows_of(plan, pr, inj)]), device="cuda")
+    croot = cen[torch.as_tensor(roots, device="cuda")].contiguous()
+    pr13 = bsh.post_params(T_c=pr.T_sft, T_obs=spec["T_obs"], m_a=m, m_Om=m, m_t=m, d_coinc=13.0)
+    pairs, _, _, npair = bsh.coincidences(truth, ones.double(), ones, croot,
+                                          torch.ones(roots.size, dtype=torch.float64, device="cuda"),
+                                          torch.ones(roots.size, dtype=torch.int32, device="cuda"), pr13,
+                                          cap=n_inj * max(1, roots.size))
+    npair = int(npair.item())
+    found = set(int(i) for i in pairs[:npair, 0].cpu().numpy())
+    rec = len(found)
+    E = rec / n_inj
+    plan.close()
+    return {"workload": f"metric bank: {pr.N} SFTs (2 det, 1 yr), 0.1 Hz at 200 Hz, {pr.S} sky points in "
+                        f"{len(pr.patch_start) - 1} patches, a_p 3-13 ls, P 10-20 d, mismatch {m}, "
+                        f"{pr.B} binary templates on {pr.orbit.shape[0]} orbit rows",
+            "terms": int(pr.n_terms), "count_s": t_count, "terms_per_s": pr.n_terms / t_count, "tile": tile,
+            "post_s": t_post, "candidates": int(valid.sum().item()), "clusters": int(roots.size),
+            "injections": n_inj, "amplitude_over_sqrt_Sn": depth_amp, "recovered_within_13_bins": rec,
+            "efficiency": E, "efficiency_error": math.sqrt(E * (1 - E) / n_inj)}
+
+
+def _id_lists(plan, pr, ids):
+    """Candidate lists holding the given template ids at rank 0 of their patches' regions
+    (one id per region slot; later ids of the same patch go to further ranks)."""
+    import torch
+    regions = plan.regions
+    per = max(1, len(ids))
+    raw = np.zeros((regions, per), dtype=bsh.CAND_DTYPE)
+    cnt = np.zeros(regions, np.int32)
+    per_s = pr.B * pr.n_f0
+    for tid in ids:
+        s = tid // per_s
+        r = int(np.searchsorted(pr.patch_start, s, side="right") - 1)
+        raw[r, cnt[r]]["template_id"] = tid
+        cnt[r] += 1
+    return (torch.as_tensor(raw.view(np.uint8).reshape(regions, per, 32), device="cuda"),
+            torch.as_tensor(cnt, device="cuda"))
+
+
+def _rows_of(plan, pr, ids):
+    """Row of each id in the output of cand_params over _id_lists(ids)."""
+    per = max(1, len(ids))
+    per_s = pr.B * pr.n_f0
+    cnt = {}
+    rows = []
+    for tid in ids:
+        s = tid // per_s
+        r = int(np.searchsorted(pr.patch_start, s, side="right") - 1)
+        k = cnt.get(r, 0)
+        cnt[r] = k + 1
+        rows.append(r * per + k)
+    return rows
+
+
 def _lut_case(pr, n_sky_dense: int, steps: int) -> dict:
     import torch
     dp = bsh.DeviceProblem(pr, w_dtype="f16")
@@ -268,7 +385,8 @@ def lut(n_sky: int = 2000, steps: int = 3, n_sky_dense: int = 4) -> dict:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["precision", "batching", "full", "lut"])
+    ap.add_argument("what", choices=["precision", "batching", "full", "lut", "metric"])
+    ap.add_argument("--mismatch", type=float, default=6.4)
     ap.add_argument("--sky", type=int, default=0)
     ap.add_argument("--patches", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2)
@@ -286,6 +404,9 @@ def main(argv=None):
         r = batching(n_patch=a.patches, steps=a.steps)
     elif a.what == "lut":
         r = lut(n_sky=a.sky or 2000)
+    elif a.what == "metric":
+        r = metric(n_sky=a.sky or 2000, n_inj=a.injections if a.injections != 100 else 20, depth_amp=a.amp,
+                   m=a.mismatch)
     else:
         r = full(n_sky=a.sky or 100048, n_inj=a.injections, depth_amp=a.amp, n_f0=a.f0)
     print(json.dumps(r))
