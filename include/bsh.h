@@ -280,6 +280,22 @@ int bsh_power_sum(bsh_plan* plan, bsh_cand* cands, const int32_t* n_cands, int n
                   bsh_cand* final_list, int32_t* n_final, bsh_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* (v') Stage 2 on another SFT set, Sec. IV.C: the power sums of Eq. (26) of */
+/* plan `stage1`'s candidate lists computed with the SFTs of plan `stage2`   */
+/* -- the stage-1 SFTs together with the complementary SFTs that start T_c/2 */
+/* later (where T_c contiguous seconds of data exist), about twice as many.  */
+/* stage2's problems must search the same templates as stage1's (same sky    */
+/* points in the same patches, binary templates, F0 and n_f0; checked on the */
+/* host except for the sky values) and carry rho.  cands / n_cands as written */
+/* by bsh_toplist on stage1 (stride stage1's top_k); n_cf <= stage1's top_k; */
+/* final_list [regions][n_cf], n_final [regions] as for bsh_power_sum.      */
+/* stage2 is a BATCHED plan that needs no bsh_number_count: its track tables */
+/* are computed here.  Capturable.                                           */
+/* ------------------------------------------------------------------------ */
+int bsh_power_sum_sft(bsh_plan* stage2, const bsh_plan* stage1, bsh_cand* cands, const int32_t* n_cands, int n_cf,
+                      bsh_cand* final_list, int32_t* n_final, bsh_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* CUDA-graph form of (iii)+(iv)+(v): the first call records the three calls */
 /* on `stream` into a graph owned by the plan, later calls replay it.         */
 /* Arguments as for bsh_toplist and bsh_power_sum; changing them requires     */

@@ -134,6 +134,8 @@ _SIGS = {
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_cluster_workspace": (ctypes.c_size_t, [ctypes.c_int]),
+    "bsh_power_sum_sft": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_cluster": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -352,6 +354,13 @@ class Plan:
         self._final_buffers(n_cf)
         _check(lib().bsh_power_sum(self.h, _ptr(self.cands), _ptr(self.n_cands), n_cf, _ptr(self.final),
                                    _ptr(self.n_final), _stream(stream)), "bsh_power_sum")
+        return self.final, self.n_final
+
+    def power_sum_sft(self, stage1: "Plan", n_cf: int, stream=None):
+        """bsh_power_sum_sft: stage 2 of stage1's lists with this plan's SFTs (the sliding set)."""
+        self._final_buffers(n_cf)
+        _check(lib().bsh_power_sum_sft(self.h, stage1.h, _ptr(stage1.cands), _ptr(stage1.n_cands), n_cf,
+                                       _ptr(self.final), _ptr(self.n_final), _stream(stream)), "bsh_power_sum_sft")
         return self.final, self.n_final
 
     def graph_launch(self, n_cf: int, stream=None):

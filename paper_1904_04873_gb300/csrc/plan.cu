@@ -1004,6 +1004,40 @@ int bsh_power_sum(bsh_plan* p, bsh_cand* cands, const int32_t* n_cands, int n_cf
     return cuda_fail(cudaGetLastError());
 }
 
+int bsh_power_sum_sft(bsh_plan* p2, const bsh_plan* p1, bsh_cand* cands, const int32_t* n_cands, int n_cf,
+                      bsh_cand* final_list, int32_t* n_final, bsh_stream stream) {
+    if (!p2 || !p1 || !p2->bound) return BSH_ERR_STATE;
+    if (!cands || !n_cands || !final_list || !n_final || n_cf < 1 || n_cf > p1->top_k) return BSH_ERR_ARG;
+    if (p2->mode != BSH_MODE_BATCHED || p2->n != p1->n || p2->regions != p1->regions) return BSH_ERR_ARG;
+    for (int q = 0; q < p2->n; ++q) {
+        const ProbHost& a = p1->P[q];
+        const ProbHost& b = p2->P[q];
+        // the same templates: sky count, patches, binary templates and f0 grid
+        if (!b.d.rho || a.pd.S != b.pd.S || a.pd.B != b.pd.B || a.pd.n_f0 != b.pd.n_f0 || a.pd.F0 != b.pd.F0 ||
+            a.ps != b.ps || a.orb != b.orb || a.brow != b.brow || a.bap != b.bap ||
+            a.pd.region_base != b.pd.region_base)
+            return BSH_ERR_ARG;
+    }
+    unsigned* sp = status_ptr();
+    if (!sp) return BSH_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ProbDev* dprobs = reinterpret_cast<const ProbDev*>(p2->ws + p2->off_probs);
+    for (int q = 0; q < p2->n; ++q) launch_tables(p2->P[q].pd, dprobs + q, p2->mode, sp, st);
+    PowerArgs a{};
+    a.probs = dprobs;
+    a.n_probs = p2->n;
+    a.region_problem = reinterpret_cast<const int32_t*>(p2->ws + p2->off_rprob);
+    a.cands = cands;
+    a.n_cands = n_cands;
+    a.top_k = p1->top_k;
+    a.n_cf = n_cf;
+    a.final_list = final_list;
+    a.n_final = n_final;
+    a.status = sp;
+    launch_power(a, p2->regions, st);
+    return cuda_fail(cudaGetLastError());
+}
+
 int bsh_graph_reset(bsh_plan* p) {
     if (!p) return BSH_ERR_ARG;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);

@@ -386,6 +386,131 @@ def attach_bank(pr: Problem, orbit, bank_orbit, bank_ap) -> Problem:
                                bank_ap=np.asarray(bank_ap, dtype=np.float64))
 
 
+@dataclasses.dataclass
+class TimeSeries:
+    """Complex baseband data of one band for each detector, in contiguous segments.
+
+    Sample n of a segment starting at t0 is taken at t0 + n T_sft / M; M = 2 K samples
+    per SFT length, so that a T_sft / 2 offset is a whole number of samples.  The
+    discrete Fourier transform of M consecutive samples puts band bin k_lo + m at
+    index m (m < K).  Noise: complex white Gaussian with E|x|^2 = S_n / M, so that an
+    SFT bin has mean power S_n.
+    """
+    T_sft: float
+    k_lo: int
+    K: int
+    M: int
+    dets: List[str]
+    Sn: List[float]
+    seg_start: List[np.ndarray]     # per detector: start time of each segment (s)
+    seg_len: List[np.ndarray]       # per detector: whole SFTs in each segment
+    x: List[List[np.ndarray]]       # per detector, per segment: samples [seg_len * M]
+
+    def sample_times(self, d: int, g: int) -> np.ndarray:
+        return self.seg_start[d][g] + np.arange(self.x[d][g].size) * (self.T_sft / self.M)
+
+
+def time_series(n_per_det: int, dets: List[str], T_sft: float, span: float, k_lo: int, K: int,
+                seg_sfts=(8, 40), seed: int = SEED_NOISE, sn_ratio: float = 1.25) -> TimeSeries:
+    """Seeded noise data: each detector's n_per_det SFT lengths of data cut into contiguous
+    segments of seg_sfts SFTs (uniform), placed at random over the span without overlap."""
+    rng = np.random.default_rng(seed)
+    M = 2 * K
+    starts, lens, xs, Sns = [], [], [], []
+    for d, _ in enumerate(dets):
+        L = []
+        left = n_per_det
+        while left > 0:
+            m = int(min(left, rng.integers(seg_sfts[0], seg_sfts[1] + 1)))
+            L.append(m)
+            left -= m
+        L = np.array(L, dtype=np.int64)
+        total = float(L.sum()) * T_sft
+        gaps = rng.random(L.size + 1)
+        gaps *= (span - total) / gaps.sum()
+        st = -0.5 * span + np.cumsum(gaps[:-1]) + np.concatenate([[0.0], np.cumsum(L[:-1] * T_sft)])
+        Sn = 1.0 if d == 0 else sn_ratio
+        seg = []
+        for m in L:
+            n = int(m) * M
+            seg.append((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * math.sqrt(Sn / (2.0 * M)))
+        starts.append(st)
+        lens.append(L)
+        xs.append(seg)
+        Sns.append(Sn)
+    return TimeSeries(T_sft=T_sft, k_lo=k_lo, K=K, M=M, dets=list(dets), Sn=Sns, seg_start=starts, seg_len=lens,
+                      x=xs)
+
+
+def inject_series(ts: TimeSeries, freq_bins, amp: float, phase: float = 0.0) -> None:
+    """Adds a unit-amplitude-per-SFT-bin signal whose instantaneous frequency, in bins, is
+    freq_bins(d, t) (detector index, times); amp scales its SFT-bin amplitude to amp sqrt(S_n)."""
+    for d in range(len(ts.dets)):
+        A = amp * math.sqrt(ts.Sn[d]) / ts.M
+        for g in range(len(ts.x[d])):
+            t = ts.sample_times(d, g)
+            f = np.asarray(freq_bins(d, t), dtype=np.float64) - ts.k_lo
+            ph = phase + 2.0 * math.pi * np.concatenate([[0.0], np.cumsum(f[:-1])]) / ts.M
+            ts.x[d][g] = ts.x[d][g] + A * np.exp(1j * ph)
+
+
+def _sfts(ts: TimeSeries, sliding: bool):
+    """(mid-times, detector index, powers [n][K]) of the SFTs of the data: every whole SFT of
+    each segment, or with sliding=True the SFTs starting T_sft/2 later (where a whole SFT
+    length of data follows)."""
+    tm, det, pw = [], [], []
+    off = ts.M // 2 if sliding else 0
+    for d in range(len(ts.dets)):
+        for g, L in enumerate(ts.seg_len[d]):
+            x = ts.x[d][g]
+            for k in range(int(L) - (1 if sliding else 0)):
+                a = k * ts.M + off
+                X = np.fft.fft(x[a:a + ts.M])
+                pw.append((X[:ts.K].real ** 2 + X[:ts.K].imag ** 2).astype(np.float32))
+                tm.append(ts.seg_start[d][g] + (k + 0.5) * ts.T_sft + off * ts.T_sft / ts.M)
+                det.append(d)
+    return np.array(tm), np.array(det, dtype=np.int32), np.array(pw)
+
+
+def sliding_problems(n_per_det: int = 120, n_sky: int = 6, patch_size: int = 3, n_ap: int = 3, n_P: int = 2,
+                     n_T: int = 2, f_lo: float = 200.0, n_f0: int = 90, span: float = 30 * DAY,
+                     T_sft: float = 900.0, seg_sfts=(6, 20), seed: int = SEED_NOISE, top_k: int = 50,
+                     inject=None):
+    """Stage-1 and stage-2 SFT sets from one time series (Sec. IV.C): the stage-1 problem
+    holds every whole SFT of the data, the stage-2 problem those plus the SFTs shifted by
+    T_sft / 2.  Both search the same sky (patches of patch_size), binary grid (a_p 0.5-10 ls,
+    P 15-45 d) and f0 bins.  inject(ts, pr1) may add signals to the data before the SFTs
+    are taken.  Returns (pr1, pr2, ts)."""
+    dets = ["H1", "L1"]
+    sky = fibonacci_sky(n_sky)
+    a_p = np.linspace(0.5, 10.0, n_ap)
+    Omega = 2.0 * math.pi / (np.linspace(15.0, 45.0, n_P) * DAY)
+    F0 = math.floor(f_lo * T_sft)
+    tt = np.linspace(-0.5 * span, 0.5 * span, 4001)
+    v_max = max(float(np.max(np.linalg.norm(detector_velocity(tt, d), axis=1))) for d in dets) * (1 + 1e-9)
+    k_lo, K, W = band_for(F0, F0 + n_f0 - 1, v_max, float(a_p.max()), float(Omega.max()), min_K=101)
+    ts = time_series(n_per_det, dets, T_sft, span, k_lo, K, seg_sfts=seg_sfts, seed=seed)
+
+    def problem(name, tm, det, pw):
+        v = np.concatenate([detector_velocity(tm[det == d], dn) for d, dn in enumerate(dets)])
+        arms = np.concatenate([detector_arms(tm[det == d], dn) for d, dn in enumerate(dets)])
+        order = np.concatenate([np.nonzero(det == d)[0] for d in range(len(dets))])
+        Sn = np.array([ts.Sn[d] for d in det[order]])
+        return Problem(name=name, T_sft=T_sft, t=tm[order], v=v, arms=arms, Sn=Sn, det=det[order], sky=sky,
+                       patch_start=_patches(sky.shape[0], patch_size), a_p=a_p, Omega=Omega,
+                       T_asc=_tasc_grid(Omega, n_T), F0=float(F0), n_f0=int(n_f0), k_lo=k_lo, K=K, W=W,
+                       power=pw[order], median_window=101, top_k=top_k)
+
+    tm0, det0, _ = _sfts(ts, False)
+    if inject is not None:
+        inject(ts, problem("plan", tm0, det0, np.zeros((tm0.size, K), np.float32)))
+    tm1, det1, pw1 = _sfts(ts, False)
+    tm2, det2, pw2 = _sfts(ts, True)
+    pr1 = problem("stage1", tm1, det1, pw1)
+    pr2 = problem("stage2", np.concatenate([tm1, tm2]), np.concatenate([det1, det2]), np.concatenate([pw1, pw2]))
+    return pr1, pr2, ts
+
+
 def precision_stress(n_sky: int = 2000, n_per_det: int = 2000, n_ap: int = 32, n_P: int = 32,
                      n_T: int = 32, seed: int = SEED_NOISE) -> Problem:
     """Mid workload on the half-bin f0 grid (F = k + 1/2), detector velocities
