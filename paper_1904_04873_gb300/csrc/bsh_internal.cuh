@@ -220,7 +220,8 @@ __host__ __device__ __forceinline__ bool fp_window_ends(int v0, int v1, int pbas
     const long long B31 = 31LL * Bc, V0 = 31LL * v0;
     // jc = first j with V_j on the far side of 31 Bc; estimated in single precision
     // (error below one step) and settled with exact integer comparisons
-    const float est = (float)(B31 - V0) / (float)d;
+    // (32-bit operands: Bc - v0 and v1 - v0 lie within two cells, |.| < 2^31)
+    const float est = (31.0f * (float)((int)Bc - v0)) / (float)(v1 - v0);
     int jc = (int)ceilf(est);
     jc = jc < 0 ? 0 : (jc > 32 ? 32 : jc);
     for (int it = 0; it < 2; ++it) {
