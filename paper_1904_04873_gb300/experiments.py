@@ -214,7 +214,7 @@ def full(n_sky: int = 100048, n_inj: int = 100, depth_amp: float = 0.5, top_k: i
             "efficiency_error": math.sqrt(E * (1 - E) / n_inj)}
 
 
-def metric(n_sky: int = 2000, n_inj: int = 20, depth_amp: float = 0.5, m: float = 6.4, ap_block: float = 2.0,
+def metric(n_sky: int = 2000, n_inj: int = 20, depth_amp: float = 0.5, m: float = 6.4, ap_block=None,
            n_cf: int = 100, seed: int = synth.SEED_INJ) -> dict:
     """Bank search with injections, stage 2 and GPU post-processing."""
     import torch
@@ -286,7 +286,7 @@ def metric(n_sky: int = 2000, n_inj: int = 20, depth_amp: float = 0.5, m: float 
                         f"{len(pr.patch_start) - 1} patches, a_p 3-13 ls, P 10-20 d, mismatch {m}, "
                         f"{pr.B} binary templates on {pr.orbit.shape[0]} orbit rows",
             "terms": int(pr.n_terms), "count_s": t_count, "terms_per_s": pr.n_terms / t_count, "tile": tile,
-            "post_s": t_post, "candidates": int(valid.sum().item()), "clusters": int(roots.size),
+            "ap_block": spec["ap_block"], "post_s": t_post, "candidates": int(valid.sum().item()), "clusters": int(roots.size),
             "injections": n_inj, "amplitude_over_sqrt_Sn": depth_amp, "recovered_within_13_bins": rec,
             "efficiency": E, "efficiency_error": math.sqrt(E * (1 - E) / n_inj)}
 
@@ -387,6 +387,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["precision", "batching", "full", "lut", "metric"])
     ap.add_argument("--mismatch", type=float, default=6.4)
+    ap.add_argument("--ap-block", type=float, default=None)
     ap.add_argument("--sky", type=int, default=0)
     ap.add_argument("--patches", type=int, default=64)
     ap.add_argument("--steps", type=int, default=2)
@@ -406,7 +407,7 @@ def main(argv=None):
         r = lut(n_sky=a.sky or 2000)
     elif a.what == "metric":
         r = metric(n_sky=a.sky or 2000, n_inj=a.injections if a.injections != 100 else 20, depth_amp=a.amp,
-                   m=a.mismatch)
+                   m=a.mismatch, ap_block=a.ap_block)
     else:
         r = full(n_sky=a.sky or 100048, n_inj=a.injections, depth_amp=a.amp, n_f0=a.f0)
     print(json.dumps(r))

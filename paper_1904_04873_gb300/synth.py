@@ -368,15 +368,17 @@ def metric(n_sky: int = 2000, n_per_det: int = 2000, ap_range=(3.0, 13.0), P_day
                         seed=seed, top_k=top_k)
 
 
-def metric_spec(pr: Problem, m: float = 6.4, ap_block: float = 2.0) -> dict:
+def metric_spec(pr: Problem, m: float = 6.4, ap_block: Optional[float] = None) -> dict:
     """Bank parameters for a metric() problem: spacings at the band's top frequency,
     T_obs the span of the SFTs, t_asc around the mid-time (t = 0), equal mismatch
-    parameters m for a_p, Omega and t_asc."""
+    parameters m for a_p, Omega and t_asc; ap_block None = one a_p block per Omega
+    (every a_p of an Omega shares its t_asc grid)."""
     f_top = (pr.F0 + pr.n_f0 - 1) / pr.T_sft
     T_obs = float(pr.t.max() - pr.t.min()) + pr.T_sft
-    return dict(f=f_top, T_c=pr.T_sft, T_obs=T_obs, t_mid=0.0, ap_min=float(pr.a_p.min()),
-                ap_max=float(pr.a_p.max()), P_min=2.0 * math.pi / float(pr.Omega.max()),
-                P_max=2.0 * math.pi / float(pr.Omega.min()), m_a=m, m_Om=m, m_t=m, ap_block=ap_block)
+    a0, a1 = float(pr.a_p.min()), float(pr.a_p.max())
+    return dict(f=f_top, T_c=pr.T_sft, T_obs=T_obs, t_mid=0.0, ap_min=a0, ap_max=a1,
+                P_min=2.0 * math.pi / float(pr.Omega.max()), P_max=2.0 * math.pi / float(pr.Omega.min()),
+                m_a=m, m_Om=m, m_t=m, ap_block=(a1 / a0) if ap_block is None else ap_block)
 
 
 def attach_bank(pr: Problem, orbit, bank_orbit, bank_ap) -> Problem:
