@@ -440,6 +440,9 @@ def main():
                 "terms_per_s": count_rate, "count_ms": count_s * 1e3}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
+    # the bit-level ceiling: one peakgram bit (1/8 B) of shared memory per term
+    roofline["bit_ceiling"] = {"terms_per_s": n_sm * 128.0 * 8.0 * f_max,
+                               "frac": count_rate / (n_sm * 128.0 * 8.0 * f_max)}
     # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the thread
     # instructions per term that ncu measured for this kernel variant
     ipt, ipt_src = profile_value("count_batched_small_full.md",

@@ -1,6 +1,8 @@
 """Full-size sampled parity on the benchmark workload (mid: 2 x 2000 SFTs,
 2000 sky points in 40 patches, 32^3 binary templates, 90 f0 bins, top-1000),
-in the launch configuration bench.py times (autotuned batched plan).
+in the launch configuration bench.py times (autotuned batched plan), and on the
+shapes of the other workloads (full scale with stage 2, multi-band batching,
+the eccentric grid, a metric template bank).
 
 The oracle cannot count 5.9e9 templates, so it recomputes sampled outputs
 one template at a time: toplist entries (counts, s_H, P), and random
@@ -154,3 +156,35 @@ def test_batching_shape_multi_band():
         _sampled_check(dp.pr, op, wq, lists, plan.first_region(q), rng, n_patch_check=1, n_entries=15,
                        n_random=40)
     plan.close()
+
+
+def test_eccentric_workload_shape():
+    # the eccentric bench workload's construction (16^3 x 3 x 3 ELL1 grid), 4 patches of its sky
+    pr = synth.eccentric(n_sky=200, patch_size=50)
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    plan.autotune()
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(100)
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    plan.close()
+    _sampled_check(pr, op, wq, lists, 0, np.random.default_rng(13), n_patch_check=2, n_entries=20, n_random=60)
+
+
+def test_metric_bank_workload_shape():
+    # the metric experiment's bank (a_p 3-13 ls, P 10-20 d, mismatch 6.4, one a_p block per Omega)
+    from oracle import bank as obank
+    pr = synth.metric(n_sky=150, patch_size=50)
+    pr = synth.attach_bank(pr, *obank.template_bank(**synth.metric_spec(pr, m=6.4)))
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    plan.autotune()
+    plan.number_count()
+    cands, n = plan.toplist()
+    plan.power_sum(100)
+    assert bsh.sync_status() == bsh.OK
+    lists = bsh.cands_to_numpy(cands, n)
+    plan.close()
+    _sampled_check(pr, op, wq, lists, 0, np.random.default_rng(14), n_patch_check=2, n_entries=20, n_random=60)
