@@ -181,7 +181,7 @@ typedef struct bsh_problem {
 } bsh_problem;
 
 typedef struct bsh_count_options {
-    int mode;                  /* BSH_MODE_BATCHED or BSH_MODE_PLAIN */
+    int mode;                  /* BSH_MODE_BATCHED, BSH_MODE_PLAIN or BSH_MODE_LUT */
     int top_k;                 /* toplist length per patch (N_C of Sec. IV.C), 1..16384 */
     int threads;               /* CTA size: 0 = autotuned / default, else 128 or 256 */
     int sft_chunk;             /* SFTs per shared-memory stage: 0 = default, else 64, 128 or 256 */
@@ -192,7 +192,8 @@ typedef struct bsh_plan bsh_plan;
 
 /* Validates the problems on the host, picks the fixed-point scales and the
  * static persistent schedule.  HOST only, no CUDA call.  patch_start and the
- * grid arrays are copied; device pointers are stored and used by later calls.
+ * grid or bank arrays are copied; device pointers are stored and used by later
+ * calls.
  * Returns BSH_ERR_RANGE when the band does not cover every track, when a
  * parameter leaves the fixed-point range, or when a patch holds 2^32 or more
  * templates. */
@@ -234,6 +235,15 @@ int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas)
  * not capturable. */
 int bsh_plan_set_accumulate(bsh_plan* plan, int variant);
 int bsh_plan_accumulate(const bsh_plan* plan);
+
+/* How the batched kernels form the fixed-point binary term: 0 = per warp from the staged
+ * tables (the default when many templates share an orbit row), 1 = per term from the
+ * thread's orbit row (the default when a warp's templates span more than 4 rows, as in
+ * metric banks; the predicated-add accumulation is then used), -1 = automatic.  Rebuilds
+ * the schedule like bsh_plan_set_accumulate; not capturable.  bsh_plan_direct returns the
+ * choice in effect. */
+int bsh_plan_set_direct(bsh_plan* plan, int mode);
+int bsh_plan_direct(const bsh_plan* plan);
 
 /* ------------------------------------------------------------------------ */
 /* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */

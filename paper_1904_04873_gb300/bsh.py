@@ -130,6 +130,8 @@ _SIGS = {
     "bsh_debug_track_windows": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_void_p, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_binary_resolution": (ctypes.c_int, [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3),
+    "bsh_plan_set_direct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "bsh_plan_direct": (ctypes.c_int, [ctypes.c_void_p]),
     "bsh_cand_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -369,6 +371,11 @@ class Plan:
                                       _ptr(self.n_final), _stream(stream)), "bsh_graph_launch")
         return self.final, self.n_final
 
+    def set_direct(self, mode: int):
+        """bsh_plan_set_direct: -1 automatic, 0 per-warp C values, 1 per-term C values."""
+        _check(lib().bsh_plan_set_direct(self.h, mode), "bsh_plan_set_direct")
+        return lib().bsh_plan_direct(self.h)
+
     def autotune(self, stream=None):
         _check(lib().bsh_autotune(self.h, _stream(stream)), "bsh_autotune")
         return self.tile()
@@ -377,7 +384,7 @@ class Plan:
         t, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().bsh_plan_tile(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g)), "bsh_plan_tile")
         return {"threads": t.value, "sft_chunk": c.value, "ctas": g.value,
-                "accumulate": lib().bsh_plan_accumulate(self.h)}
+                "accumulate": lib().bsh_plan_accumulate(self.h), "direct": lib().bsh_plan_direct(self.h)}
 
     def set_accumulate(self, variant: int):
         _check(lib().bsh_plan_set_accumulate(self.h, variant), "bsh_plan_set_accumulate")

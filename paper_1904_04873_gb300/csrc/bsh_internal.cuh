@@ -320,6 +320,7 @@ struct CountArgs {
     int wrows;                   // Omega-T rows one warp needs at most
     int acc_mode;                // weighted accumulation variant of the batched kernel
     int lut;                     // 1: look-up-table approximation of the track (BSH_MODE_LUT)
+    int direct;                  // 1: C_q formed per term from the staged rows (predicated-add only)
 };
 
 struct TmapSet {

@@ -104,7 +104,9 @@ struct Layout {
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
 
-__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc) {
+// direct: the C values are formed per term from the staged c_q rows (no per-warp arrays).
+__host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc,
+                                              int direct) {
     Layout L;
     const int nw = threads / 32;
     int o = 0;
@@ -114,8 +116,8 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + I * ot_max * 4); }
     L.y = o; o = align128(o + nw * I * 8);
     L.ye = o; o = align128(o + nw * I * 8);
-    L.cp = o; o = align128(o + nw * I * wrows * 4);
-    L.ce = o; o = align128(o + nw * I * wrows * 8);
+    L.cp = o; o = align128(o + (direct ? 0 : nw * I * wrows * 4));
+    L.ce = o; o = align128(o + (direct ? 0 : nw * I * wrows * 8));
     L.acc = o; o = align128(o + JW * threads * 4);
     L.comp = o; o = align128(o + JW * threads * 4);
     L.tab = o; o = align128(o + (acc ? nw * 256 * 4 : 0));
@@ -371,12 +373,15 @@ __device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, 
 // that byte j holds template j's 8 bits).
 // LUT = true: the look-up-table approximation of Sec. IV.B -- every template of an f0
 // block reads the window at the block's reference template's modulation.
-template <int THREADS, int NE, int ACC, bool LUT>
+// DIRECT = true: each thread forms C_q from its orbit row's staged c_q entry per term
+// instead of reading per-warp converted arrays (for banks where few templates share a
+// row and those arrays would not fit in shared memory).
+template <int THREADS, int NE, int ACC, bool LUT, bool DIRECT>
 __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     count_batched(const CountArgs a, const __grid_constant__ TmapSet maps) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NW = THREADS / 32;
-    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max, a.wrows, THREADS, ACC);
+    const Layout L = make_layout(a.chunk, a.wseg_max, a.ot_max, a.wrows, THREADS, ACC, DIRECT ? 1 : 0);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar);
     unsigned* done = reinterpret_cast<unsigned*>(smem + L.done);
     SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem + L.sel);
@@ -430,6 +435,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         const int nrw = otw1 - otw0 + 1;                        // rows this warp needs (<= wrows)
         const int ot = bvalid ? P.brow[b] - otw0 : 0;
         const int orow0 = otw0 - cur.ot0;                       // their offset in the CTA's staged rows
+        const int myrow = bvalid ? P.brow[b] - cur.ot0 : 0;      // this thread's staged row (DIRECT)
         const int apq = bvalid ? P.bapq[b] : 0;
         const int s_y = P.fp.s_y, M = P.fp.M;
         const int wseg = a.wseg_max;
@@ -485,12 +491,15 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 yp[e] = make_int2(make_Z(F2ref, vq, fpl), LUT ? fpl.M : fp_margin(vq, fpl));
                 if (!LUT) ype[e] = make_int2(make_Z(F2a, vq, fpl), make_Z(F2b, vq, fpl));
             }
-            for (int e = lane; e < I * nrw; e += 32) {
-                const int r = e / I, il = e - r * I;
-                const int cq = cr[(orow0 + r) * I + il];
-                cp[il * wrows + r] = make_C(F2ref, cq, fpl);
-                if (!LUT) cpe[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
+            if (!DIRECT) {
+                for (int e = lane; e < I * nrw; e += 32) {
+                    const int r = e / I, il = e - r * I;
+                    const int cq = cr[(orow0 + r) * I + il];
+                    cp[il * wrows + r] = make_C(F2ref, cq, fpl);
+                    if (!LUT) cpe[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
+                }
             }
+            const int32_t* myc = cr + myrow * I;
             __syncwarp();
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
             const float* wt = reinterpret_cast<const float*>(smem + L.w[buf]);
@@ -502,7 +511,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 for (int u = 0; u < 8; ++u) {
                     const int il = g8 + u;
                     const int2 z = yp[il];
-                    const int v = z.x - __mulhi(apq, cp[il * wrows + ot]);
+                    const int cc = DIRECT ? make_C(F2ref, myc[il], fpl) : cp[il * wrows + ot];
+                    const int v = z.x - __mulhi(apq, cc);
                     // in the staged segment by construction (host band check, device velocity
                     // check); the clamp only keeps the read in bounds
                     const unsigned pos = min((unsigned)(pbase + (v >> s_y)), (unsigned)pos_max);
@@ -522,7 +532,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                                                      cur.j0 + (cur.jb - 1) / 2, a.status);
                             } else {
                                 const int2 ze = ype[il];
-                                const int2 ce = cpe[il * wrows + ot];
+                                const int2 ce = DIRECT ? make_int2(make_C(F2a, myc[il], fpl), make_C(F2b, myc[il], fpl))
+                                                       : cpe[il * wrows + ot];
                                 const int v0 = ze.x - __mulhi(apq, ce.x);
                                 const int v1 = ze.y - __mulhi(apq, ce.y);
                                 int path;
@@ -710,9 +721,9 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
 
 }  // namespace
 
-int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc) {
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc, int direct) {
     if (mode == BSH_MODE_PLAIN) return align128((int)sizeof(SelectSmem)) + align128((int)sizeof(TopSmem));
-    return make_layout(I, wseg, ot_max, wrows, threads, acc).total;
+    return make_layout(I, wseg, ot_max, wrows, threads, acc, direct).total;
 }
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st) {
@@ -730,16 +741,17 @@ void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads
         return;
     }
     const bool small_n = a.max_n < 8 * 1024;
-#define BSH_LAUNCH_BATCHED(T, NE, ACC, LUT)                                       \
-    do {                                                                          \
-        static int s_done = 0;                                                    \
-        ensure_smem(count_batched<T, NE, ACC, LUT>, a.smem_bytes, &s_done);       \
-        count_batched<T, NE, ACC, LUT><<<grid, T, a.smem_bytes, st>>>(a, maps);   \
+#define BSH_LAUNCH_BATCHED(T, NE, ACC, LUT, DIR)                                        \
+    do {                                                                                \
+        static int s_done = 0;                                                          \
+        ensure_smem(count_batched<T, NE, ACC, LUT, DIR>, a.smem_bytes, &s_done);        \
+        count_batched<T, NE, ACC, LUT, DIR><<<grid, T, a.smem_bytes, st>>>(a, maps);    \
     } while (0)
 #define BSH_LAUNCH_ACC(T, NE, LUT)                                                \
     do {                                                                          \
-        if (a.acc_mode) BSH_LAUNCH_BATCHED(T, NE, 1, LUT);                        \
-        else BSH_LAUNCH_BATCHED(T, NE, 0, LUT);                                   \
+        if (a.direct) BSH_LAUNCH_BATCHED(T, NE, 0, LUT, true);                    \
+        else if (a.acc_mode) BSH_LAUNCH_BATCHED(T, NE, 1, LUT, false);            \
+        else BSH_LAUNCH_BATCHED(T, NE, 0, LUT, false);                            \
     } while (0)
 #define BSH_LAUNCH_NE(T, LUT)                                                     \
     do {                                                                          \

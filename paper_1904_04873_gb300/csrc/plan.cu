@@ -13,7 +13,7 @@
 #include "bsh_internal.cuh"
 
 namespace bsh {
-int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc);
+int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc, int direct);
 }
 
 using namespace bsh;
@@ -167,6 +167,8 @@ struct bsh_plan {
     size_t ws_cap = 0;                     // workspace bytes: the largest of the tuning candidates
     double tuned_rate = 0.0;
     int acc_mode = 0;                      // weighted accumulation variant (autotuned)
+    int direct_opt = -1;                   // per-term C values: -1 automatic, 0 off, 1 on
+    int direct = 0;                        // the choice in effect
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
@@ -480,6 +482,8 @@ int build_schedule(bsh_plan* p, long long item_limit) {
             }
         }
     }
+    // orbit rows shared by few templates (banks): form C per term rather than per warp
+    p->direct = p->mode == BSH_MODE_BATCHED && (p->direct_opt == 1 || (p->direct_opt < 0 && p->wrows > 4)) ? 1 : 0;
     int region = 0;
     long long items = 0;
     for (auto& h : p->P) {
@@ -496,14 +500,16 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     const int smem_two = (227 * 1024) / blocks_target - 1024, smem_one = 220 * 1024;
     const int chunk0 = p->chunk;
     while (true) {
-        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode);
+        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
+                                   p->direct);
         if (p->smem <= smem_two || p->chunk <= 32) break;
         p->chunk /= 2;
     }
     if (p->smem > smem_two) {
         p->chunk = chunk0;
         while (true) {
-            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode);
+            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
+                                   p->direct);
             if (p->smem <= smem_one || p->chunk <= 32) break;
             p->chunk /= 2;
         }
@@ -693,6 +699,7 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.mode = p->mode;
     a.wrows = p->wrows;
     a.acc_mode = p->acc_mode;
+    a.direct = p->direct;
     a.lut = p->lut;
     a.max_n = 0;
     for (auto& h : p->P) a.max_n = std::max(a.max_n, h.d.N);
@@ -903,6 +910,20 @@ int bsh_plan_set_accumulate(bsh_plan* p, int variant) {
 }
 
 int bsh_plan_accumulate(const bsh_plan* p) { return p ? p->acc_mode : -1; }
+
+int bsh_plan_set_direct(bsh_plan* p, int mode) {
+    if (!p || mode < -1 || mode > 1) return BSH_ERR_ARG;
+    p->direct_opt = mode;
+    const int rc = build_schedule(p);
+    if (rc) return rc;
+    if (p->bound) {
+        const int rc2 = upload_plan(p, nullptr);
+        if (rc2) return rc2;
+    }
+    return bsh_graph_reset(p);
+}
+
+int bsh_plan_direct(const bsh_plan* p) { return p ? p->direct : -1; }
 
 int bsh_track_precision(bsh_plan* p, int problem, int s_begin, int s_end, unsigned long long* counts,
                         bsh_stream stream) {

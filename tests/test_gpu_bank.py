@@ -105,3 +105,55 @@ def test_library_bank_drives_the_same_search():
     orc_bank = obank.template_bank(**spec)
     for x, y in zip(lib_bank, orc_bank):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kind", ["grid", "bank"])
+@pytest.mark.parametrize("direct", [0, 1])
+def test_per_term_and_per_warp_binary_terms(kind, direct):
+    # both ways of forming the fixed-point binary term, on a grid (many templates per orbit row)
+    # and on a metric bank (few)
+    if kind == "grid":
+        pr = small_mid(n_sky=6, n_per_det=150, n_ap=4, n_P=3, n_T=3, patch_size=3, top_k=40)
+    else:
+        pr = metric_slice(rows=(300, 700))
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    assert plan.set_direct(direct) == direct
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    check_dense(gu[0], gw[0], op.count_dense())
+    plan.number_count()
+    assert bsh.sync_status() == bsh.OK
+    _, sc = oracle_scores(op, wq)
+    by_patch = [sc[pr.patch_start[p]:pr.patch_start[p + 1]] for p in range(len(pr.patch_start) - 1)]
+    check_toplists(plan, dp, 0, by_patch, pr.top_k, tol=2e-4)
+    plan.close()
+
+
+def test_bank_defaults_to_per_term_terms():
+    pr = metric_slice(rows=(0, 600), ap_block=2.0)
+    dp, _, _ = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    assert plan.tile()["direct"] == 1
+    plan.close()
+    pr = small_mid(n_sky=6, n_per_det=150, n_ap=32, n_P=2, n_T=2, patch_size=3, top_k=40)
+    dp, _, _ = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    assert plan.tile()["direct"] == 0
+    plan.close()
+
+
+def test_per_term_binary_terms_with_the_lut():
+    import oracle
+    pr = metric_slice(rows=(300, 700))
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_LUT, top_k=pr.top_k)
+    assert plan.tile()["direct"] == 1
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    nb = -(-pr.n_f0 // 32)
+    lut = oracle.OracleProblem(bits=op.bits, w=op.w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky,
+                               a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K, orbit=pr.orbit,
+                               bank_orbit=pr.bank_orbit, bank_ap=pr.bank_ap, lut_block=-(-pr.n_f0 // nb))
+    check_dense(gu[0], gw[0], lut.count_dense())
+    plan.close()
