@@ -20,6 +20,13 @@ Parity status per function (each pinned by ``tests/test_oracle_*.py``):
   significance    pinned (Monte-Carlo mean / variance of Bernoulli peakgrams)
   toplist         pinned (full numpy lexsort)
   power sum       pinned (rho = 1 gives sum w; linearity; single-bin rho)
+  LUT count       pinned (block of one and zero modulation reduce to the exact track;
+                  reference templates exact; shift direction; departure rate vs |(j - j_ref) D|)
+  explicit banks  pinned (a grid written out as a bank counts the same)
+  bank.py         pinned (Eq. (30)-(32) scalings, layout and spacings, coverage, the
+                  paper's template-count scaling)
+  postprocess.py  pinned (distance identities, scipy connected components, chains, cut /
+                  centroid / best cluster, coincidences, ecliptic projection)
 """
 from __future__ import annotations
 
