@@ -149,3 +149,60 @@ def test_peakgram_and_weights_argument_errors():
     assert L.bsh_make_peakgram(1 << 20, 4, 100, 0, 1.6, None, 1 << 20, 3, None) == bsh.ERR_ARG
     assert L.bsh_make_peakgram(1 << 20, 4, 200, 100, 1.6, None, 1 << 20, 8, None) == bsh.ERR_ARG
     assert L.bsh_weights(1 << 20, 3, 1 << 20, 1 << 20, 10, 1, 9, 1 << 20, None, None, None) == bsh.ERR_ARG
+
+
+def test_bank_and_eccentric_plans_on_the_host(small):
+    # explicit banks and eccentric grids are validated and planned without a GPU
+    from oracle import bank as obank
+    fp = FakeProblem(small)
+    kap = np.array([-0.05, 0.0, 0.05])
+    fk = FakeProblem(small, n_kappa=3, kappa=kap.ctypes.data, n_eta=1, eta=kap[1:2].ctypes.data)
+    rc, h = create([fk.d])
+    assert rc == bsh.OK
+    bsh.lib().bsh_plan_destroy(h)
+    bad = np.array([0.7])
+    rc, _ = create([FakeProblem(small, n_kappa=1, kappa=bad.ctypes.data).d])
+    assert rc == bsh.ERR_ARG
+    pr = synth.metric(n_sky=4, n_per_det=40, patch_size=2)
+    orbit, bo, ba = obank.template_bank(**synth.metric_spec(pr, m=6.4))
+    fb = FakeProblem(pr, n_orbit=orbit.shape[0], orbit=orbit.ctypes.data, n_bank=bo.size,
+                     bank_orbit=bo.ctypes.data, bank_ap=ba.ctypes.data)
+    rc, h = create([fb.d])
+    assert rc == bsh.OK
+    L = bsh.lib()
+    assert L.bsh_plan_direct(h) == 1          # warps span many orbit rows
+    assert L.bsh_plan_set_direct(h, 2) == bsh.ERR_ARG
+    assert L.bsh_plan_set_direct(h, 0) == bsh.OK and L.bsh_plan_direct(h) == 0
+    L.bsh_plan_destroy(h)
+    # a bank whose rows decrease, or that points past its rows, is refused
+    bo2 = bo.copy()
+    bo2[[0, 1]] = bo2[[1, 0]] + np.array([5, 0], np.int32)
+    fb2 = FakeProblem(pr, n_orbit=orbit.shape[0], orbit=orbit.ctypes.data, n_bank=bo2.size,
+                      bank_orbit=bo2.ctypes.data, bank_ap=ba.ctypes.data)
+    assert create([fb2.d])[0] == bsh.ERR_ARG
+    bo3 = bo.copy()
+    bo3[-1] = orbit.shape[0]
+    fb3 = FakeProblem(pr, n_orbit=orbit.shape[0], orbit=orbit.ctypes.data, n_bank=bo3.size,
+                      bank_orbit=bo3.ctypes.data, bank_ap=ba.ctypes.data)
+    assert create([fb3.d])[0] == bsh.ERR_ARG
+
+
+def test_post_processing_argument_errors():
+    # argument checks happen on the host before anything is enqueued
+    L = bsh.lib()
+    pp = bsh.post_params()
+    fake = ctypes.c_void_p(1 << 20)
+    assert L.bsh_cluster(fake, fake, fake, (1 << 20) + 1, ctypes.byref(pp), fake, 1 << 30, fake, fake, fake,
+                         fake, fake, None) == bsh.ERR_ARG
+    assert L.bsh_cluster(fake, fake, fake, 10, None, fake, 1 << 30, fake, fake, fake, fake, fake,
+                         None) == bsh.ERR_ARG
+    assert L.bsh_cluster(fake, fake, fake, 10, ctypes.byref(pp), fake, 16, fake, fake, fake, fake, fake,
+                         None) == bsh.ERR_WORKSPACE
+    bad = bsh.post_params(T_c=-1.0)
+    assert L.bsh_coincidences(fake, fake, fake, 5, fake, fake, fake, 5, ctypes.byref(bad), fake, 1 << 20, fake,
+                              fake, fake, 10, fake, None) == bsh.ERR_ARG
+    assert L.bsh_cluster_workspace(1000) >= 1000 * 120
+    assert L.bsh_coincidence_workspace(10, 20) >= 30 * 48
+    assert L.bsh_cand_params(None, 0, fake, fake, 10, 0, ctypes.byref(pp), fake, fake, fake, None) == \
+        bsh.ERR_STATE
+    assert L.bsh_power_sum_sft(None, None, fake, fake, 10, fake, fake, None) == bsh.ERR_STATE
