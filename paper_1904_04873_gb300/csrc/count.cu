@@ -99,10 +99,12 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 // per-thread Kahan sums, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, ye, cp, ce, acc, comp, tab, bar, done, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, ye, cp, ce, sl, acc, comp, tab, bar, done, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
+
+constexpr int SCAP = 8;   // deferred near-boundary entries per thread and SFT chunk
 
 // direct: the C values are formed per term from the staged c_q rows (no per-warp arrays).
 __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc,
@@ -118,6 +120,7 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     L.ye = o; o = align128(o + nw * I * 8);
     L.cp = o; o = align128(o + (direct ? 0 : nw * I * wrows * 4));
     L.ce = o; o = align128(o + (direct ? 0 : nw * I * wrows * 8));
+    L.sl = o; o = align128(o + SCAP * threads);
     L.acc = o; o = align128(o + JW * threads * 4);
     L.comp = o; o = align128(o + JW * threads * 4);
     L.tab = o; o = align128(o + (acc ? nw * 256 * 4 : 0));
@@ -395,6 +398,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     int2* ype = reinterpret_cast<int2*>(smem + L.ye) + warp * I;     // Z at j0, j0 + 31
     int* cp = reinterpret_cast<int*>(smem + L.cp) + warp * I * wrows;            // C at the reference
     int2* cpe = reinterpret_cast<int2*>(smem + L.ce) + warp * I * wrows;         // C at j0, j0 + 31
+    uint8_t* slist = reinterpret_cast<uint8_t*>(smem + L.sl);                     // [SCAP][THREADS]
     float* tab = reinterpret_cast<float*>(smem + L.tab) + warp * 256;
 
     long long it = a.cta_item[blockIdx.x];
@@ -504,6 +508,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
             const float* wt = reinterpret_cast<const float*>(smem + L.w[buf]);
             const int i0 = ch * I;
+            int scnt = 0;                 // deferred entries of this thread in this chunk
             for (int g8 = 0; g8 < I; g8 += 8) {
                 uint32_t mk[8];
                 unsigned slow = 0u;
@@ -519,11 +524,26 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     mk[u] = row_window(pk + il * wseg, (int)pos);
                     slow |= (fp_fast_ref(v, z.y, s_y) ? 0u : 1u) << u;
                 }
-                if (slow) {       // rare: near a rounding boundary; each lane takes its next entry
-                    unsigned sl = slow;
-                    while (sl) {
-                        const int u = __ffs(sl) - 1;
-                        sl &= sl - 1u;
+                if (slow) {       // rare: near a rounding boundary
+                    unsigned now = 0u;
+                    if (!LUT) {
+                        // defer to the chunk's end, where the lanes resolve them together
+                        unsigned sl = slow;
+                        while (sl) {
+                            const int u = __ffs(sl) - 1;
+                            sl &= sl - 1u;
+                            if (scnt < SCAP) slist[scnt++ * THREADS + tid] = (uint8_t)(g8 + u);
+                            else now |= 1u << u;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if ((slow >> k) & 1u) mk[k] = 0u;
+                    } else {
+                        now = slow;
+                    }
+                    while (now) {
+                        const int u = __ffs(now) - 1;
+                        now &= now - 1u;
                         const int il = g8 + u;
                         uint32_t wv = 0u;
                         if (bvalid && i0 + il < P.N) {
@@ -604,6 +624,41 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     eights = t;
                 }
                 if ((g8 & 63) == 56) kahan_fold<THREADS>(part, sacc, scomp, tid);   // every 64 SFTs
+            }
+            if (!LUT) {
+                // the chunk's deferred entries: each lane its own, all lanes at once
+                const int npass = __reduce_max_sync(0xffffffffu, scnt);
+                for (int k = 0; k < npass; ++k) {
+                    if (k >= scnt) continue;
+                    const int il = slist[k * THREADS + tid];
+                    uint32_t m = 0u;
+                    if (bvalid && i0 + il < P.N) {
+                        const int2 ze = ype[il];
+                        const int2 ce = DIRECT ? make_int2(make_C(F2a, myc[il], fpl), make_C(F2b, myc[il], fpl))
+                                               : cpe[il * wrows + ot];
+                        const int v0 = ze.x - __mulhi(apq, ce.x);
+                        const int v1 = ze.y - __mulhi(apq, ce.y);
+                        int path;
+                        if (!fp_window_ends(v0, v1, pbase, pos_max, s_y, M, pk + il * wseg, &m, &path))
+                            m = slow_window_exact(P, v0, v1, pbase, pos_max, pk + il * wseg, cur.s, b, i0 + il,
+                                                  cur.j0, a.status);
+                    }
+                    const float wv = wt[il];
+#pragma unroll
+                    for (int j = 0; j < JW; ++j)
+                        if (m & (1u << j)) part[j] += wv;
+                    // one more mask into the bit-sliced counters
+                    uint32_t c = m, t;
+                    t = ones & c; ones ^= c; c = t;
+                    t = twos & c; twos ^= c; c = t;
+                    t = fours & c; fours ^= c; c = t;
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) {
+                        t = e8[q] & c;
+                        e8[q] ^= c;
+                        c = t;
+                    }
+                }
             }
             // done with this buffer: the last warp to finish refills it two chunks ahead
             __syncwarp();
