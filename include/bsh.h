@@ -232,7 +232,9 @@ int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas)
  * compensation across 64-SFT blocks).  bsh_plan_set_accumulate re-derives
  * the SFT stage for the variant's shared-memory layout, re-uploads a bound
  * plan (synchronising the legacy default stream) and drops a recorded graph;
- * not capturable. */
+ * not capturable.  A plan that forms its binary terms per term (bsh_plan_direct
+ * = 1) keeps variant 0; there the autotuner's second candidate per shape is one
+ * CTA per SM with the stage left unshrunk instead. */
 int bsh_plan_set_accumulate(bsh_plan* plan, int variant);
 int bsh_plan_accumulate(const bsh_plan* plan);
 

@@ -92,7 +92,7 @@ struct ProbDev {
     int G0;                   // floor(F0)
     int JB;                   // valid templates per f0 block (<= 32)
     int n_fb, n_bt;           // f0 blocks, binary tiles
-    int ot_tile;              // Omega-T rows staged per binary tile
+    int crows;                // orbit rows per staged box of c_q (batched mode)
     FixedPoint fp;
     int o_min, o_max;         // bounds of floor(v / 2^s_y)
     int Wseg;                 // staged words per row
@@ -323,8 +323,11 @@ struct CountArgs {
     int direct;                  // 1: C_q formed per term from the staged rows (predicated-add only)
 };
 
+// TMA descriptors of the batched kernel, one pair per problem: the peakgram rows and
+// the fixed-point orbit table c_q.
 struct TmapSet {
     alignas(64) unsigned char map[MAX_PROBLEMS][128];
+    alignas(64) unsigned char cmap[MAX_PROBLEMS][128];
 };
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st);

@@ -106,6 +106,12 @@ __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~12
 
 constexpr int SCAP = 8;   // deferred near-boundary entries per thread and SFT chunk
 
+// Row stride (32-bit words) of the staged c_q rows: the chunk plus four words, so that
+// threads of a warp reading one SFT of up to 8 consecutive orbit rows hit distinct
+// shared-memory banks (the TMA box of the table is this wide; a 256-SFT chunk, at the
+// box limit, is not padded).
+__host__ __device__ __forceinline__ int c_stride(int I) { return I < 256 ? I + 4 : I; }
+
 // direct: the C values are formed per term from the staged c_q rows (no per-warp arrays).
 __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc,
                                               int direct) {
@@ -115,7 +121,7 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     for (int b = 0; b < 2; ++b) { L.pk[b] = o; o = align128(o + I * wseg * 4); }
     for (int b = 0; b < 2; ++b) { L.vn[b] = o; o = align128(o + I * 4); }
     for (int b = 0; b < 2; ++b) { L.w[b] = o; o = align128(o + I * 4); }
-    for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + I * ot_max * 4); }
+    for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + c_stride(I) * ot_max * 4); }
     L.y = o; o = align128(o + nw * I * 8);
     L.ye = o; o = align128(o + nw * I * 8);
     L.cp = o; o = align128(o + (direct ? 0 : nw * I * wrows * 4));
@@ -180,14 +186,15 @@ __device__ __forceinline__ void issue_stage(const CountArgs& a, const TmapSet& m
     const int I = a.chunk;
     const int i0 = ch * I;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar) + buf;
-    const uint32_t bytes = (uint32_t)(I * a.wseg_max * 4 + I * 4 * 2 + c.nrows * I * 4);
+    // the c_q box holds P.crows rows from the item's first row (rows past the table
+    // are zero-filled and still count toward the expected bytes)
+    const uint32_t bytes = (uint32_t)(I * a.wseg_max * 4 + I * 4 * 2 + c_stride(I) * P.crows * 4);
     fence_proxy_async();
     mbar_arrive_expect_tx(bar, bytes);
     tma_load_2d(smem + L.pk[buf], maps.map[c.q], bar, c.c0, i0);
+    tma_load_2d(smem + L.c[buf], maps.cmap[c.q], bar, i0, c.ot0);
     bulk_load(smem + L.vn[buf], P.vn_q + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
     bulk_load(smem + L.w[buf], P.w32 + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
-    for (int r = 0; r < c.nrows; ++r)
-        bulk_load(smem + L.c[buf] + r * I * 4, P.c_q + (size_t)(c.ot0 + r) * P.Np + i0, (uint32_t)(I * 4), bar);
 }
 
 // 8 x 8 bit-matrix transpose: byte u of x is row u (bit k = column k); on
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         bool aborted = false;
         for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
             const int buf = g & 1;
-            if (!mbar_wait(&bars[buf], (g >> 1) & 1)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[buf], (g >> 1) & 1))) {   // warp-uniform exit
                 if (lane == 0) {
                     set_status(a.status, ST_TIMEOUT);
                     ts.abort = 1;
@@ -498,12 +505,12 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
             if (!DIRECT) {
                 for (int e = lane; e < I * nrw; e += 32) {
                     const int r = e / I, il = e - r * I;
-                    const int cq = cr[(orow0 + r) * I + il];
+                    const int cq = cr[(orow0 + r) * c_stride(I) + il];
                     cp[il * wrows + r] = make_C(F2ref, cq, fpl);
                     if (!LUT) cpe[il * wrows + r] = make_int2(make_C(F2a, cq, fpl), make_C(F2b, cq, fpl));
                 }
             }
-            const int32_t* myc = cr + myrow * I;
+            const int32_t* myc = cr + myrow * c_stride(I);
             __syncwarp();
             const uint32_t* pk = reinterpret_cast<const uint32_t*>(smem + L.pk[buf]);
             const float* wt = reinterpret_cast<const float*>(smem + L.w[buf]);
@@ -775,6 +782,8 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
 }
 
 }  // namespace
+
+int count_c_stride(int I) { return c_stride(I); }
 
 int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc, int direct) {
     if (mode == BSH_MODE_PLAIN) return align128((int)sizeof(SelectSmem)) + align128((int)sizeof(TopSmem));

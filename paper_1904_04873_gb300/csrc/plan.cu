@@ -14,6 +14,7 @@
 
 namespace bsh {
 int count_smem_bytes(int mode, int I, int wseg, int ot_max, int wrows, int threads, int acc, int direct);
+int count_c_stride(int I);
 }
 
 using namespace bsh;
@@ -169,6 +170,7 @@ struct bsh_plan {
     int acc_mode = 0;                      // weighted accumulation variant (autotuned)
     int direct_opt = -1;                   // per-term C values: -1 automatic, 0 off, 1 on
     int direct = 0;                        // the choice in effect
+    int one_cta = 0;                       // 1: one CTA per SM with the unshrunk stage (autotuned)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
@@ -426,10 +428,11 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     int first_rc = -1;
     for (int t : tune_threads(p))
         for (int c : tune_chunks(p))
-            for (int am = 0; am < 2; ++am) {
+            for (int v = 0; v < 4; ++v) {
                 p->threads = t;
                 p->chunk = c;
-                p->acc_mode = am;
+                p->acc_mode = v & 1;
+                p->one_cta = v >> 1;
                 const int rc = build_schedule(p);
                 if (first_rc < 0) first_rc = rc;
                 if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
@@ -437,6 +440,7 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     p->threads = tune_threads(p)[0];
     p->chunk = tune_chunks(p)[0];
     p->acc_mode = 0;
+    p->one_cta = 0;
     const int rc = build_schedule(p);
     if (rc) {
         delete p;
@@ -484,6 +488,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     }
     // orbit rows shared by few templates (banks): form C per term rather than per warp
     p->direct = p->mode == BSH_MODE_BATCHED && (p->direct_opt == 1 || (p->direct_opt < 0 && p->wrows > 4)) ? 1 : 0;
+    if (p->direct) p->acc_mode = 0;   // the per-term variant accumulates by predicated adds only
     int region = 0;
     long long items = 0;
     for (auto& h : p->P) {
@@ -495,17 +500,21 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     }
     p->regions = region;
     // chunk size: shrink until the CTAs that the register budget allows per SM
-    // (512 threads) also fit its shared memory; else settle for one CTA per SM
+    // (512 threads) also fit its shared memory; else (or when one CTA per SM is
+    // asked for) settle for one CTA per SM
     const int blocks_target = 512 / p->threads;
     const int smem_two = (227 * 1024) / blocks_target - 1024, smem_one = 220 * 1024;
     const int chunk0 = p->chunk;
-    while (true) {
+    const bool one = p->one_cta || p->opt.ctas_per_sm == 1;
+    bool fits_two = false;
+    while (!one) {
         p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
                                    p->direct);
-        if (p->smem <= smem_two || p->chunk <= 32) break;
+        fits_two = p->smem <= smem_two;
+        if (fits_two || p->chunk <= 32) break;
         p->chunk /= 2;
     }
-    if (p->smem > smem_two) {
+    if (!fits_two) {
         p->chunk = chunk0;
         while (true) {
             p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
@@ -528,7 +537,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     const long long all_items = items;
     const long long total_items = item_limit >= 0 ? std::min(item_limit, all_items) : all_items;
     const int cps = p->opt.ctas_per_sm ? p->opt.ctas_per_sm
-                    : (p->mode == BSH_MODE_BATCHED && p->smem <= smem_two ? blocks_target : 1);
+                    : (p->mode == BSH_MODE_BATCHED && fits_two ? blocks_target : 1);
     const int k = p->top_k;
     // region item ranges
     std::vector<long long> r_begin(p->regions + 1, 0);
@@ -675,6 +684,15 @@ int encode_bits_map(bsh_plan* p, int q) {
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(h.d.bits), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return BSH_ERR_ARG;
+    // the fixed-point orbit table c_q [nOT][Np]: a box of crows rows x (chunk + pad) SFTs
+    const ProbDev& pd = h.pd;
+    CUtensorMap* mc = reinterpret_cast<CUtensorMap*>(p->maps.cmap[q]);
+    cuuint64_t cdims[2] = {(cuuint64_t)pd.Np, (cuuint64_t)pd.nOT};
+    cuuint64_t cstrides[1] = {(cuuint64_t)pd.Np * 4};
+    cuuint32_t cbox[2] = {(cuuint32_t)count_c_stride(p->chunk), (cuuint32_t)pd.crows};
+    r = enc(mc, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, pd.c_q, cdims, cstrides, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? BSH_OK : BSH_ERR_ARG;
 }
 
@@ -731,7 +749,8 @@ int run_count(bsh_plan* p, int dense, cudaStream_t st) {
 
 namespace {
 // Points the descriptors at the workspace under the current layout, encodes the
-// peakgram tensor maps and uploads the small tables; synchronises `st`.
+// TMA descriptors (peakgram rows, fixed-point orbit table) and uploads the small
+// tables; synchronises `st`.
 int upload_plan(bsh_plan* p, cudaStream_t st) {
     std::vector<ProbDev> hp(p->n);
     for (int q = 0; q < p->n; ++q) {
@@ -755,6 +774,7 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
         pd.vn_q = reinterpret_cast<int32_t*>(p->ws + h.off_vnq);
         pd.c_q = reinterpret_cast<int32_t*>(p->ws + h.off_cq);
         pd.c64 = reinterpret_cast<double*>(p->ws + h.off_c64);
+        pd.crows = std::min(p->ot_max, pd.nOT);
         if (p->mode == BSH_MODE_PLAIN) {
             pd.w64 = reinterpret_cast<double*>(p->ws + h.off_w);
             pd.w32 = nullptr;
@@ -809,7 +829,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     const std::vector<int> ths = tune_threads(p), chs = tune_chunks(p);
     if (ths.size() * chs.size() <= 1) return BSH_OK;
     double best_rate = -1.0;
-    int best_t = p->threads, best_c = p->chunk, best_a = p->acc_mode;
+    int best_t = p->threads, best_c = p->chunk, best_a = p->acc_mode, best_o = p->one_cta;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return BSH_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -821,14 +841,17 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     for (int t : ths) {
         for (int c : chs) {
           for (int am = 0; am < 2; ++am) {
+            // the second variant: the byte-table accumulation, or for the per-term binary
+            // variant (predicated adds only) one CTA per SM with the unshrunk stage
             p->threads = t;
             p->chunk = c;
-            p->acc_mode = am;
+            p->acc_mode = p->direct ? 0 : am;
+            p->one_cta = p->direct ? am : 0;
             // a slice of the work list: about sixteen items per CTA of this shape
             const long long slice = (long long)p->num_sms * (512 / t) * 16;
             if (build_schedule(p, slice) != BSH_OK || p->ws_size > p->ws_cap) continue;
             // the stage may have been shrunk to fit shared memory: time each effective shape once
-            const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | am;
+            const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | (p->acc_mode << 1) | p->one_cta;
             if (std::find(tried.begin(), tried.end(), key) != tried.end()) continue;
             tried.push_back(key);
             if ((rc = upload_plan(p, st)) != BSH_OK) break;
@@ -865,7 +888,8 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 best_rate = rate;
                 best_t = t;
                 best_c = c;
-                best_a = am;
+                best_a = p->acc_mode;
+                best_o = p->one_cta;
             }
           }
           if (rc != BSH_OK) break;
@@ -877,6 +901,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     p->threads = best_t;
     p->chunk = best_c;
     p->acc_mode = best_a;
+    p->one_cta = best_o;
     const int rc2 = build_schedule(p);
     if (rc2 != BSH_OK) return rc2;
     const int rc3 = upload_plan(p, st);
@@ -899,6 +924,7 @@ int bsh_plan_tile(const bsh_plan* p, int* threads, int* sft_chunk, int* ctas) {
 int bsh_plan_set_accumulate(bsh_plan* p, int variant) {
     if (!p || (variant != 0 && variant != 1)) return BSH_ERR_ARG;
     p->acc_mode = variant;
+    p->one_cta = 0;
     p->chunk = tune_chunks(p)[0];
     const int rc = build_schedule(p);
     if (rc) return rc;
@@ -914,6 +940,7 @@ int bsh_plan_accumulate(const bsh_plan* p) { return p ? p->acc_mode : -1; }
 int bsh_plan_set_direct(bsh_plan* p, int mode) {
     if (!p || mode < -1 || mode > 1) return BSH_ERR_ARG;
     p->direct_opt = mode;
+    p->one_cta = 0;
     const int rc = build_schedule(p);
     if (rc) return rc;
     if (p->bound) {

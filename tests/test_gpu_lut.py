@@ -69,9 +69,11 @@ def test_lut_tile_shapes_and_accumulation():
     pr = _fast_binaries()
     dp, op, wq = device_problem(pr, "f16")
     d_lut = lut_oracle(pr, op).count_dense()
-    for threads, chunk, acc in ((128, 64, 1), (256, 256, 0)):
+    for threads, chunk, acc, direct in ((128, 64, 1, 0), (256, 256, 0, 0), (256, 64, 0, 1)):
         plan = bsh.Plan([dp], bsh.MODE_LUT, top_k=pr.top_k, threads=threads, sft_chunk=chunk)
+        plan.set_direct(direct)
         plan.set_accumulate(acc)
+        assert plan.tile()["accumulate"] == acc and plan.tile()["direct"] == direct
         gu, gw = plan.count_dense()
         assert bsh.sync_status() == bsh.OK
         check_dense(gu[0], gw[0], d_lut)

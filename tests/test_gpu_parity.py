@@ -100,17 +100,34 @@ def test_count_dense_batched(mid_small, dtype):
     plan.close()
 
 
-@pytest.mark.parametrize("threads,chunk,acc", [(128, 64, 0), (256, 256, 0), (128, 256, 1), (256, 64, 1),
-                                               (256, 128, 1)])
-def test_count_dense_tile_shapes(mid_small, threads, chunk, acc):
+@pytest.mark.parametrize("threads,chunk,acc,direct", [(128, 64, 0, 1), (256, 256, 0, 1), (256, 64, 0, 0),
+                                                      (128, 256, 1, 0), (256, 64, 1, 0), (256, 128, 1, 0)])
+def test_count_dense_tile_shapes(mid_small, threads, chunk, acc, direct):
+    # every accumulation variant and both ways of forming the binary term (the byte-table
+    # accumulation exists only with the per-warp term)
     pr = mid_small
     dp, op, wq = device_problem(pr, "f16")
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=chunk)
+    plan.set_direct(direct)
     plan.set_accumulate(acc)
-    assert plan.tile()["threads"] == threads and plan.tile()["accumulate"] == acc
+    t = plan.tile()
+    assert t["threads"] == threads and t["accumulate"] == acc and t["direct"] == direct
     gu, gw = plan.count_dense()
     assert bsh.sync_status() == bsh.OK
     check_dense(gu[0], gw[0], op.count_dense())
+    plan.close()
+
+
+def test_per_term_plans_keep_predicated_adds(mid_small):
+    pr = mid_small
+    dp, _, _ = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    assert plan.set_direct(1) == 1
+    plan.set_accumulate(1)
+    assert plan.tile()["accumulate"] == 0
+    plan.set_direct(0)
+    plan.set_accumulate(1)
+    assert plan.tile()["accumulate"] == 1 and plan.tile()["direct"] == 0
     plan.close()
 
 
