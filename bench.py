@@ -452,6 +452,9 @@ def main():
                            "frac": count_rate / (n_sm * 128.0 * f_max / ipt), "source": ipt_src}
     else:
         roofline["alu"] = {"ceiling_terms_per_s": None, "instr_per_term": None, "frac": None, "source": ipt_src}
+    # the word-gather roofline is the metric's denominator, not a hard limit of this kernel (one
+    # shared-memory word serves 32 terms); the ceilings that bind are ALU issue, then the bit level
+    roofline["binding"] = "alu" if ipt else None
 
     cpu = None
     if not args.no_cpu and rank == 0:

@@ -99,7 +99,7 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 // per-thread Kahan sums, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, ye, cp, ce, sl, acc, comp, tab, bar, done, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, cp, ce, sl, acc, comp, tab, bar, done, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
@@ -123,7 +123,6 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     for (int b = 0; b < 2; ++b) { L.w[b] = o; o = align128(o + I * 4); }
     for (int b = 0; b < 2; ++b) { L.c[b] = o; o = align128(o + c_stride(I) * ot_max * 4); }
     L.y = o; o = align128(o + nw * I * 8);
-    L.ye = o; o = align128(o + nw * I * 8);
     L.cp = o; o = align128(o + (direct ? 0 : nw * I * wrows * 4));
     L.ce = o; o = align128(o + (direct ? 0 : nw * I * wrows * 8));
     L.sl = o; o = align128(o + SCAP * threads);
@@ -402,7 +401,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     const int I = a.chunk;
     const int wrows = a.wrows;
     int2* yp = reinterpret_cast<int2*>(smem + L.y) + warp * I;       // Z at the reference, margin
-    int2* ype = reinterpret_cast<int2*>(smem + L.ye) + warp * I;     // Z at j0, j0 + 31
     int* cp = reinterpret_cast<int*>(smem + L.cp) + warp * I * wrows;            // C at the reference
     int2* cpe = reinterpret_cast<int2*>(smem + L.ce) + warp * I * wrows;         // C at j0, j0 + 31
     uint8_t* slist = reinterpret_cast<uint8_t*>(smem + L.sl);                     // [SCAP][THREADS]
@@ -493,14 +491,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 break;
             }
             // this warp's track values for the chunk: Z at the reference template with the SFT's
-            // margin (the slope bound; M alone for the LUT), C_q at the reference template, and
-            // both at the block's ends for the two-ended test
+            // margin (the slope bound; M alone for the LUT), C_q at the reference template and at
+            // the block's ends (Z at the ends is formed from the staged vn_q by the rare deferred
+            // entries that need it)
             const int32_t* vnr = reinterpret_cast<const int32_t*>(smem + L.vn[buf]);
             const int32_t* cr = reinterpret_cast<const int32_t*>(smem + L.c[buf]);
             for (int e = lane; e < I; e += 32) {
                 const int vq = vnr[e];
                 yp[e] = make_int2(make_Z(F2ref, vq, fpl), LUT ? fpl.M : fp_margin(vq, fpl));
-                if (!LUT) ype[e] = make_int2(make_Z(F2a, vq, fpl), make_Z(F2b, vq, fpl));
             }
             if (!DIRECT) {
                 for (int e = lane; e < I * nrw; e += 32) {
@@ -558,7 +556,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                                 wv = slow_window_lut(P, pbase, pos_max, pk + il * wseg, cur.s, b, i0 + il,
                                                      cur.j0 + (cur.jb - 1) / 2, a.status);
                             } else {
-                                const int2 ze = ype[il];
+                                const int2 ze = make_int2(make_Z(F2a, vnr[il], fpl), make_Z(F2b, vnr[il], fpl));
                                 const int2 ce = DIRECT ? make_int2(make_C(F2a, myc[il], fpl), make_C(F2b, myc[il], fpl))
                                                        : cpe[il * wrows + ot];
                                 const int v0 = ze.x - __mulhi(apq, ce.x);
@@ -640,7 +638,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     const int il = slist[k * THREADS + tid];
                     uint32_t m = 0u;
                     if (bvalid && i0 + il < P.N) {
-                        const int2 ze = ype[il];
+                        const int2 ze = make_int2(make_Z(F2a, vnr[il], fpl), make_Z(F2b, vnr[il], fpl));
                         const int2 ce = DIRECT ? make_int2(make_C(F2a, myc[il], fpl), make_C(F2b, myc[il], fpl))
                                                : cpe[il * wrows + ot];
                         const int v0 = ze.x - __mulhi(apq, ce.x);
