@@ -216,10 +216,11 @@ int bsh_plan_bind(bsh_plan* plan, void* workspace, size_t bytes, bsh_stream stre
 
 /* Runs the autotuner: times the candidate tile shapes (CTA size 256 or 128
  * binary templates, 64 / 128 / 256 SFTs per shared-memory stage, unless fixed
- * by the options, and the two weighted-accumulation variants) on a slice of
- * the work list of about sixteen items per CTA, best of three runs each,
- * keeps the fastest and re-uploads the plan.  Synchronises; not capturable;
- * drops a recorded graph. */
+ * by the options; both ways of forming the binary term unless fixed by
+ * bsh_plan_set_direct; per way, the two weighted-accumulation variants, or for
+ * the per-term way one or two CTAs per SM) on a slice of the work list of
+ * about sixteen items per CTA, best of three runs each, keeps the fastest and
+ * re-uploads the plan.  Synchronises; not capturable; drops a recorded graph. */
 int bsh_autotune(bsh_plan* plan, bsh_stream stream);
 
 /* Current tile shape: CTA size, SFTs per stage, persistent CTAs in the grid. */

@@ -170,6 +170,7 @@ struct bsh_plan {
     int acc_mode = 0;                      // weighted accumulation variant (autotuned)
     int direct_opt = -1;                   // per-term C values: -1 automatic, 0 off, 1 on
     int direct = 0;                        // the choice in effect
+    int direct_tuned = -1;                 // the autotuner's choice under direct_opt = -1 (-1: none yet)
     int one_cta = 0;                       // 1: one CTA per SM with the unshrunk stage (autotuned)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
@@ -428,11 +429,12 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     int first_rc = -1;
     for (int t : tune_threads(p))
         for (int c : tune_chunks(p))
-            for (int v = 0; v < 4; ++v) {
+            for (int v = 0; v < 8; ++v) {
                 p->threads = t;
                 p->chunk = c;
                 p->acc_mode = v & 1;
-                p->one_cta = v >> 1;
+                p->one_cta = (v >> 1) & 1;
+                p->direct_tuned = v >> 2;
                 const int rc = build_schedule(p);
                 if (first_rc < 0) first_rc = rc;
                 if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
@@ -441,6 +443,7 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     p->chunk = tune_chunks(p)[0];
     p->acc_mode = 0;
     p->one_cta = 0;
+    p->direct_tuned = -1;
     const int rc = build_schedule(p);
     if (rc) {
         delete p;
@@ -487,7 +490,8 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         }
     }
     // orbit rows shared by few templates (banks): form C per term rather than per warp
-    p->direct = p->mode == BSH_MODE_BATCHED && (p->direct_opt == 1 || (p->direct_opt < 0 && p->wrows > 4)) ? 1 : 0;
+    const bool auto_direct = p->direct_tuned >= 0 ? p->direct_tuned == 1 : p->wrows > 4;
+    p->direct = p->mode == BSH_MODE_BATCHED && (p->direct_opt == 1 || (p->direct_opt < 0 && auto_direct)) ? 1 : 0;
     if (p->direct) p->acc_mode = 0;   // the per-term variant accumulates by predicated adds only
     int region = 0;
     long long items = 0;
@@ -829,7 +833,9 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     const std::vector<int> ths = tune_threads(p), chs = tune_chunks(p);
     if (ths.size() * chs.size() <= 1) return BSH_OK;
     double best_rate = -1.0;
-    int best_t = p->threads, best_c = p->chunk, best_a = p->acc_mode, best_o = p->one_cta;
+    int best_t = p->threads, best_c = p->chunk, best_a = p->acc_mode, best_o = p->one_cta, best_d = p->direct_tuned;
+    // under the automatic choice both ways of forming the binary term are candidates
+    const int n_dir = p->mode == BSH_MODE_BATCHED && p->direct_opt < 0 ? 2 : 1;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return BSH_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -840,18 +846,25 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     std::vector<long long> tried;
     for (int t : ths) {
         for (int c : chs) {
-          for (int am = 0; am < 2; ++am) {
-            // the second variant: the byte-table accumulation, or for the per-term binary
-            // variant (predicated adds only) one CTA per SM with the unshrunk stage
+          for (int v = 0; v < 2 * n_dir; ++v) {
+            // per way of forming the binary term, a second variant: the byte-table accumulation,
+            // or for the per-term binary variant (predicated adds only) one CTA per SM with the
+            // unshrunk stage
+            const int am = v & 1;
             p->threads = t;
             p->chunk = c;
-            p->acc_mode = p->direct ? 0 : am;
-            p->one_cta = p->direct ? am : 0;
+            if (n_dir == 2) p->direct_tuned = v >> 1;
+            // the way build_schedule will take (p->wrows does not depend on the tile shape)
+            const bool dir = p->direct_opt == 1 ||
+                             (p->direct_opt < 0 && (p->direct_tuned >= 0 ? p->direct_tuned == 1 : p->wrows > 4));
+            p->acc_mode = dir ? 0 : am;
+            p->one_cta = dir ? am : 0;
             // a slice of the work list: about sixteen items per CTA of this shape
             const long long slice = (long long)p->num_sms * (512 / t) * 16;
             if (build_schedule(p, slice) != BSH_OK || p->ws_size > p->ws_cap) continue;
             // the stage may have been shrunk to fit shared memory: time each effective shape once
-            const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | (p->acc_mode << 1) | p->one_cta;
+            const long long key = ((long long)t << 32) | ((long long)p->chunk << 4) | (p->direct << 2) |
+                                  (p->acc_mode << 1) | p->one_cta;
             if (std::find(tried.begin(), tried.end(), key) != tried.end()) continue;
             tried.push_back(key);
             if ((rc = upload_plan(p, st)) != BSH_OK) break;
@@ -890,6 +903,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 best_c = c;
                 best_a = p->acc_mode;
                 best_o = p->one_cta;
+                best_d = p->direct_tuned;
             }
           }
           if (rc != BSH_OK) break;
@@ -902,6 +916,7 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
     p->chunk = best_c;
     p->acc_mode = best_a;
     p->one_cta = best_o;
+    p->direct_tuned = best_d;
     const int rc2 = build_schedule(p);
     if (rc2 != BSH_OK) return rc2;
     const int rc3 = upload_plan(p, st);
@@ -940,6 +955,7 @@ int bsh_plan_accumulate(const bsh_plan* p) { return p ? p->acc_mode : -1; }
 int bsh_plan_set_direct(bsh_plan* p, int mode) {
     if (!p || mode < -1 || mode > 1) return BSH_ERR_ARG;
     p->direct_opt = mode;
+    p->direct_tuned = -1;
     p->one_cta = 0;
     const int rc = build_schedule(p);
     if (rc) return rc;
