@@ -36,7 +36,7 @@ KERNELS_PER_STEP = 8   # peakgram, weights, 2 table kernels, count, merge, power
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["mid", "small", "eccentric"], default="mid")
@@ -351,7 +351,8 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    count_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / args.steps
+    count_ms = [a.elapsed_time(b) for a, b in ev]
+    count_s = sum(count_ms) / 1e3 / args.steps
     st = bsh.sync_status()
     if st != bsh.OK:
         raise SystemExit(f"device status {st} in timed region")
@@ -437,7 +438,8 @@ def main():
                 "kernel": "bsh_number_count (track tables + count_batched)",
                 "peak_source": f"derived: {n_sm} SMs x 32 banks x 4 B/clk x {f_max / 1e6:.0f} MHz "
                                f"(MEASURED_PEAKS sm_max_mhz); one 32-bit word per term",
-                "terms_per_s": count_rate, "count_ms": count_s * 1e3}
+                "terms_per_s": count_rate, "count_ms": count_s * 1e3,
+                "count_ms_median": float(np.median(count_ms)) if count_ms else None}
     if clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = count_rate / (n_sm * 32.0 * clocks["sm_mhz"] * 1e6)
     # the bit-level ceiling: one peakgram bit (1/8 B) of shared memory per term
