@@ -130,6 +130,20 @@ def test_per_term_and_per_warp_binary_terms(kind, direct):
     plan.close()
 
 
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_one_cta_per_sm_keeps_the_stage(chunk):
+    # ctas_per_sm = 1 keeps the asked-for stage (no shrinking to fit two CTAs) and the same counts
+    pr = metric_slice(rows=(100, 500))
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=256, sft_chunk=chunk, ctas_per_sm=1)
+    t = plan.tile()
+    assert t["sft_chunk"] == chunk and t["ctas"] <= torch.cuda.get_device_properties(0).multi_processor_count
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    check_dense(gu[0], gw[0], op.count_dense())
+    plan.close()
+
+
 def test_bank_defaults_to_per_term_terms():
     pr = metric_slice(rows=(0, 600), ap_block=2.0)
     dp, _, _ = device_problem(pr, "f16")
