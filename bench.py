@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "small", "eccentric"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "small", "eccentric", "metric", "metric-small"], default="mid")
     ap.add_argument("--graph", action="store_true", help="replay count+toplist+power as one CUDA graph")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -52,23 +52,37 @@ def parse():
     return ap.parse_args()
 
 
-def make_problem(kind: str, rank: int):
+def make_problem(kind: str, rank: int, bank_fn=None):
+    """The workload's problem; `bank_fn(**spec)` generates the metric workloads' binary bank
+    (the library's generator on the GPU arm, the oracle's in the reference arm)."""
     from paper_1904_04873_gb300 import synth
-    sky = rank_sky(synth.fibonacci_sky(200 if kind == "small" else 2000), rank)
+    sky = rank_sky(synth.fibonacci_sky(200 if kind in ("small", "metric-small") else 2000), rank)
     if kind == "mid":
         return synth.mid(sky=sky)
     if kind == "eccentric":
         return synth.eccentric(sky=sky)
+    if kind in ("metric", "metric-small"):
+        return metric_problem(sky, bank_fn)
     return synth.mid(n_sky=200, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky)
 
 
-def plain_sample(kind: str, sky: np.ndarray):
+def metric_problem(sky: np.ndarray, bank_fn):
+    """The mid construction over a_p 3-13 ls, P 10-20 d searching the template bank of
+    Eq. (30)-(32) at mismatch 6.4, one a_p block per Omega."""
+    from paper_1904_04873_gb300 import synth
+    pr = synth.metric(sky=sky)
+    return synth.attach_bank(pr, *bank_fn(**synth.metric_spec(pr, m=6.4)))
+
+
+def plain_sample(kind: str, sky: np.ndarray, bank_fn=None):
     """The first 4 sky points of the workload, for the plain-form sample."""
     from paper_1904_04873_gb300 import synth
     if kind == "mid":
         return synth.mid(sky=sky[:4], patch_size=50)
     if kind == "eccentric":
         return synth.eccentric(sky=sky[:4])
+    if kind in ("metric", "metric-small"):
+        return metric_problem(sky[:4], bank_fn)
     return synth.mid(n_sky=4, n_per_det=500, n_ap=16, n_P=16, n_T=16, sky=sky[:4])
 
 
@@ -104,12 +118,18 @@ def weak_value(terms_per_rank: float, world: int, t_max: float) -> float:
 
 
 def workload_config(pr, kind):
-    binary = f"{pr.a_p.size}x{pr.Omega.size}x{pr.T_asc.shape[1]}"
-    if pr.kappa is not None:
-        binary += (f"x{pr.kappa.size}x{pr.eta.size} ELL1 (kappa, eta in +-{float(np.max(np.abs(pr.kappa))):g})")
+    if pr.bank_orbit is not None:
+        binary = (f"metric bank (Eq. (30)-(32), mismatch 6.4, a_p {pr.a_p.min():g}-{pr.a_p.max():g} ls, "
+                  f"P {2 * math.pi / pr.Omega.max() / 86400:.0f}-{2 * math.pi / pr.Omega.min() / 86400:.0f} d) "
+                  f"of {pr.B} binaries on {pr.orbit.shape[0]} orbit rows")
+    else:
+        binary = f"{pr.a_p.size}x{pr.Omega.size}x{pr.T_asc.shape[1]}"
+        if pr.kappa is not None:
+            binary += (f"x{pr.kappa.size}x{pr.eta.size} ELL1 (kappa, eta in +-{float(np.max(np.abs(pr.kappa))):g})")
+        binary += " binary"
     return {"workload": f"{kind}: {pr.N} SFTs (2 det, T_c=900 s, 1 yr), band {pr.F0 / 900.0:.1f}-"
                         f"{(pr.F0 + pr.n_f0) / 900.0:.1f} Hz, {pr.S} sky pts in patches of 50, "
-                        f"{binary} binary, {pr.n_f0} f0, top-{pr.top_k}",
+                        f"{binary}, {pr.n_f0} f0, top-{pr.top_k}",
             "templates": int(pr.n_templates), "terms_per_step": int(pr.n_terms), "weights": "fp16",
             "l2": "256 MiB L2 flush write between steps"}
 
@@ -206,18 +226,27 @@ def measured_peaks():
 
 def _oracle_worker(args):
     """Spawned process: time the oracle on binary templates [b0, b1) of sky point 0."""
-    (bits, w, v, t, F0, n_f0, sky, a_p, Om, Ta, kap, eta, k_lo, K, b0, b1) = args
+    kw, b0, b1 = args
     import sys
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
     import oracle
-    op = oracle.OracleProblem(bits=bits, w=w, v=v, t=t, F0=F0, n_f0=n_f0, sky=sky, a_p=a_p, Omega=Om,
-                              T_asc=Ta, k_lo=k_lo, K=K, kappa=kap, eta=eta)
+    op = oracle.OracleProblem(**kw)
     t0 = time.perf_counter()
     for b in range(b0, b1):
-        for j in range(n_f0):
+        for j in range(kw["n_f0"]):
             op.count_one(0, b, j)
     return time.perf_counter() - t0
+
+
+def _oracle_inputs(pr) -> dict:
+    """The oracle's problem for sky point 0 of `pr`: its own peakgram and fp16 weights."""
+    import oracle
+    rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
+    w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
+    return dict(bits=bits, w=w, v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0, sky=pr.sky[:1], a_p=pr.a_p,
+                Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo, K=pr.K, kappa=pr.kappa, eta=pr.eta,
+                orbit=pr.orbit, bank_orbit=pr.bank_orbit, bank_ap=pr.bank_ap)
 
 
 def cpu_baseline_sample(pr, budget_s: float = 12.0, procs: int = 0):
@@ -225,17 +254,13 @@ def cpu_baseline_sample(pr, budget_s: float = 12.0, procs: int = 0):
     bins, a block of binary templates per process), with one process per host
     core; returns (terms/s, cores, sample text)."""
     import multiprocessing as mp
-    import oracle
     procs = procs or (os.cpu_count() or 1)
-    rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
-    w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.kappa, pr.eta,
-            pr.k_lo, pr.K)
-    per_b = _oracle_worker(base + (0, 2)) / 2          # calibration, in this process
+    base = _oracle_inputs(pr)
+    per_b = _oracle_worker((base, 0, 2)) / 2          # calibration, in this process
     nb = max(1, min(pr.B // procs, int(budget_s / max(per_b, 1e-6))))
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        times = pool.map(_oracle_worker, [base + (q * nb, (q + 1) * nb) for q in range(procs)])
+        times = pool.map(_oracle_worker, [(base, q * nb, (q + 1) * nb) for q in range(procs)])
     dt = max(times)
     terms = procs * nb * pr.n_f0 * pr.N
     return terms / dt, procs, (f"oracle count of sky point 0 x {procs * nb} binary templates x {pr.n_f0} f0 x "
@@ -250,19 +275,16 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    pr = make_problem(args.workload, 0)
-    import oracle
+    from oracle import bank as obank
+    pr = make_problem(args.workload, 0, obank.template_bank)
     procs = os.cpu_count() or 1
-    rho, bits = oracle.peakgram(pr.power, pr.median_window, pr.rho_th, W=pr.W)
-    w = oracle.quantize(oracle.weights(pr.sky[:1], pr.arms, pr.Sn, norm=True), "f16")
-    base = (bits, w, pr.v, pr.t, pr.F0, pr.n_f0, pr.sky[:1], pr.a_p, pr.Omega, pr.T_asc, pr.kappa, pr.eta,
-            pr.k_lo, pr.K)
-    per_b = _oracle_worker(base + (0, 1))
+    base = _oracle_inputs(pr)
+    per_b = _oracle_worker((base, 0, 1))
     nb = max(1, min(pr.B // (procs * max(1, args.steps + args.warmup)), int(1.5 / max(per_b, 1e-6))))
 
     def shards(step):
         b0 = step * procs * nb
-        return [base + (b0 + q * nb, b0 + (q + 1) * nb) for q in range(procs)]
+        return [(base, b0 + q * nb, b0 + (q + 1) * nb) for q in range(procs)]
 
     with mp.get_context("spawn").Pool(procs) as pool:
         for k in range(args.warmup):
@@ -303,7 +325,7 @@ def main():
         dist.barrier()
     bsh.lib()
 
-    pr = make_problem(args.workload, rank)
+    pr = make_problem(args.workload, rank, bsh.template_bank)
     stream = torch.cuda.current_stream()
     dp = bsh.DeviceProblem(pr, w_dtype="f16")
     mode = bsh.MODE_LUT if args.track == "lut" else bsh.MODE_BATCHED
@@ -314,6 +336,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
     def step(k=None):
         flush.fill_(k if k is not None else 0)
@@ -327,7 +350,11 @@ def main():
             plan.graph_launch(n_cf)
         else:
             plan.toplist()
+            if k is not None:
+                ev2[k][0].record(stream)
             plan.power_sum(n_cf)
+            if k is not None:
+                ev2[k][1].record(stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -353,6 +380,13 @@ def main():
     elapsed = t_start.elapsed_time(t_end) / 1e3
     count_ms = [a.elapsed_time(b) for a, b in ev]
     count_s = sum(count_ms) / 1e3 / args.steps
+    stage2 = None
+    if not args.graph:
+        # stage 2 (power_kernel + rerank_kernel): every toplist entry of every patch over all SFTs
+        s2_ms = sum(a.elapsed_time(b) for a, b in ev2) / args.steps
+        n_c = int(plan.n_cands.sum().item())
+        stage2 = {"candidates": n_c, "terms": n_c * pr.N, "ms": s2_ms,
+                  "terms_per_s": n_c * pr.N / (s2_ms * 1e-3) if s2_ms > 0 else None}
     st = bsh.sync_status()
     if st != bsh.OK:
         raise SystemExit(f"device status {st} in timed region")
@@ -408,7 +442,7 @@ def main():
     # ---- plain form (FP64 track per term, FP64 weights, one launch per patch) on a bounded sample
     plain = None
     if not args.no_plain and rank == 0:
-        sub = plain_sample(args.workload, pr.sky)
+        sub = plain_sample(args.workload, pr.sky, bsh.template_bank)
         dps = bsh.DeviceProblem(sub, w_dtype="f64")
         dps.prepare()
         pplan = bsh.Plan([dps], bsh.MODE_PLAIN, top_k=pr.top_k)
@@ -447,7 +481,8 @@ def main():
                                "frac": count_rate / (n_sm * 128.0 * 8.0 * f_max)}
     # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the thread
     # instructions per term that ncu measured for this kernel variant
-    ipt, ipt_src = profile_value("count_batched_small_full.md",
+    ipt, ipt_src = profile_value("count_batched_metric_small_full.md" if args.workload.startswith("metric")
+                                 else "count_batched_small_full.md",
                                  "lut_instr_per_term" if args.track == "lut" else "instr_per_term")
     if ipt:
         roofline["alu"] = {"ceiling_terms_per_s": n_sm * 128.0 * f_max / ipt, "instr_per_term": ipt,
@@ -471,7 +506,7 @@ def main():
                                                                   "graph": bool(args.graph), "tile": tile,
                                                                   "track": args.track},
                 "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-                "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline,
+                "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roofline, "stage2": stage2,
                 "plain": plain, "cpu_baseline": cpu}
         print(json.dumps(line))
     plan.close()
