@@ -187,12 +187,17 @@ class ClockSampler:
 
 
 def kernel_sha() -> str:
-    """Short hash of the count kernel's sources (matches the ncu summaries' stamp)."""
+    """Short hash of the count kernel's sources with comments and whitespace removed, so
+    that only code changes invalidate a summary (matches the ncu summaries' stamp)."""
     import hashlib
+    import re
     src = os.path.join(ROOT, "paper_1904_04873_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
-        h.update(open(os.path.join(src, f), "rb").read())
+        text = open(os.path.join(src, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -16,8 +16,9 @@
 // j with slope D 2^s_y, so a block of 32 consecutive f0 templates [j0, j0 + 31]
 // reads one 32-bit window when v at the reference template j0 + 15, widened by
 // the margin mg = 16 |D|max 2^s_y + M, stays inside one cell; |D|max is bounded
-// per SFT from vn_q and the problem's a_p Omega bound (fp_margin).  Otherwise v
-// is evaluated at both ends of the block (fp_window_slow).
+// per SFT from vn_q and the problem's a_p Omega bound (fp_margin).  Otherwise the
+// (block, SFT) pair is deferred to the end of its SFT chunk, where v is evaluated
+// at both ends of the block (fp_window_ends, then fp_window_exact per template).
 #pragma once
 
 #include <cstdint>
@@ -172,13 +173,6 @@ __host__ __device__ __forceinline__ int fp_margin(int vn_q, const FixedPoint& fp
 // Reference-template test: v widened by mg on both sides stays in one cell.
 __host__ __device__ __forceinline__ bool fp_fast_ref(int v, int mg, int s_y) {
     return ((unsigned)((v - mg) ^ (v + mg)) >> s_y) == 0u;
-}
-
-// Fast path: both ends of the block, widened by M, fall in the same bin cell.
-__host__ __device__ __forceinline__ bool fp_fast(int v0, int v1, int s_y, int M) {
-    int lo = imin(v0, v1) - M;
-    int hi = imax(v0, v1) + M;
-    return ((unsigned)(lo ^ hi) >> s_y) == 0u;
 }
 
 // 32 consecutive bits of a staged row starting at bit position pos (0 <= pos <= 32*Wseg - 33).

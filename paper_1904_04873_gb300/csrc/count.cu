@@ -79,23 +79,31 @@ struct Item {
     int q, s, fb, bt;
 };
 
+// Item order inside a problem: its sky patches in turn; inside a patch, binary tiles,
+// then sky points, then f0 blocks (fastest).  The CTAs sharing a patch's items then walk
+// the binary tiles together, so a tile's orbit-table rows are read from L2 by every sky
+// point of the patch instead of the whole table streaming once per (sky point, f0 block).
 __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
     int q = 0;
     while (q + 1 < a.n_probs && it >= a.probs[q + 1].item_begin) ++q;
     const ProbDev& P = a.probs[q];
     const long long loc = it - P.item_begin;
     const long long per_s = (long long)P.n_fb * P.n_bt;
+    const int patch = P.patch_of_s[loc / per_s];         // a patch spans [start, end) x per_s items
+    const long long p0 = P.patch_start[patch];
+    const long long per_bt = (P.patch_start[patch + 1] - p0) * P.n_fb;
+    const long long off = loc - p0 * per_s;
     Item r;
     r.q = q;
-    r.s = (int)(loc / per_s);
-    const int rr = (int)(loc % per_s);
-    r.fb = rr / P.n_bt;
-    r.bt = rr % P.n_bt;
+    r.bt = (int)(off / per_bt);
+    const int rem = (int)(off - (long long)r.bt * per_bt);
+    r.s = (int)p0 + rem / P.n_fb;
+    r.fb = rem % P.n_fb;
     return r;
 }
 
 // Shared-memory layout of the batched kernel: double-buffered TMA stages
-// (peakgram band, vn / weight / c table rows), per-warp track pairs, the
+// (peakgram band, vn / weight / c table rows), per-warp track values, the
 // per-thread Kahan sums, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {

@@ -208,6 +208,19 @@ std::vector<int> tune_chunks(const bsh_plan* p) {
 }
 
 int build_schedule(bsh_plan* p, long long item_limit = -1);
+
+// f0 block and binary tile of item `loc` of a problem, in the batched kernel's item order:
+// patches in turn, inside a patch binary tiles, then sky points, then f0 blocks.
+void item_fb_bt(const ProbHost& h, long long loc, int* fb, int* bt) {
+    const ProbDev& pd = h.pd;
+    const long long per_s = (long long)pd.n_fb * pd.n_bt;
+    const int patch = h.patch_of_s[loc / per_s];
+    const long long p0 = h.ps[patch];
+    const long long per_bt = (h.ps[patch + 1] - p0) * pd.n_fb;
+    const long long off = loc - p0 * per_s;
+    *bt = (int)(off / per_bt);
+    *fb = (int)((off - (long long)*bt * per_bt) % pd.n_fb);
+}
 int upload_plan(bsh_plan* p, cudaStream_t st);
 
 int validate_problem(const bsh_problem& d) {
@@ -874,9 +887,8 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 int q = 0;
                 while (q + 1 < p->n && it >= p->P[q + 1].pd.item_begin) ++q;
                 const ProbDev& pd = p->P[q].pd;
-                const long long loc = it - pd.item_begin;
-                const int rr = (int)(loc % ((long long)pd.n_fb * pd.n_bt));
-                const int fb = rr / pd.n_bt, bt = rr % pd.n_bt;
+                int fb, bt;
+                item_fb_bt(p->P[q], it - pd.item_begin, &fb, &bt);
                 const int nb = std::min(t, pd.B - bt * t);
                 const int jb = std::min(pd.JB, pd.n_f0 - fb * pd.JB);
                 terms += (double)nb * jb * pd.N;
