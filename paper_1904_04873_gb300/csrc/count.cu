@@ -8,10 +8,11 @@
 // peakgram row (consecutive f0 bins, offset constant except at most one
 // boundary crossing inside the block), so one shared-memory funnel shift
 // yields 32 terms.  Unweighted counts accumulate in bit-sliced carry-save
-// counters; weighted counts in FP32 per 32-SFT block, Kahan-compensated across
-// blocks.  Persistent CTAs walk a static, cost-balanced range of items; the
-// peakgram band and the per-SFT tables of each SFT chunk are staged into
-// shared memory by TMA (cp.async.bulk.tensor / cp.async.bulk) one chunk ahead.
+// counters; weighted counts in FP32 per 64-SFT block, Kahan-compensated across
+// blocks in sums held in tensor memory (TMEM).  Persistent CTAs walk a static,
+// cost-balanced range of items; the peakgram band and the per-SFT tables of each
+// SFT chunk are staged into shared memory by TMA (cp.async.bulk.tensor /
+// cp.async.bulk) into two buffers, the next chunk loading while one is counted.
 //
 // The plain form (BSH_MODE_PLAIN) evaluates the FP64 track for every term,
 // sums FP64 weights in FP64, and runs once per sky patch.
@@ -74,6 +75,53 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// Tensor memory (TMEM) holds the per-thread Kahan sums of the weighted counts, which
+// leaves shared memory to the staged chunks.  One warp allocates the CTA's columns and
+// frees them on every exit path; a warp reaches the 32 TMEM lanes of its quarter
+// (warp index mod 4), each thread its own lane, with the 32x32b shape.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 2 consecutive columns of this thread's lane at taddr and at taddr + 32 (sum, compensation);
+// the wait is in the same statement, so no use of the values can move above it.
+__device__ __forceinline__ void tmem_ld2x2(uint32_t taddr, float* a, float* c) {
+    uint32_t r[4];
+    asm volatile(
+        "{\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%4];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%5];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n\t}"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+    a[0] = __uint_as_float(r[0]);
+    a[1] = __uint_as_float(r[1]);
+    c[0] = __uint_as_float(r[2]);
+    c[1] = __uint_as_float(r[3]);
+}
+__device__ __forceinline__ void tmem_st2x2(uint32_t taddr, const float* a, const float* c) {
+    asm volatile(
+        "{\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%4], {%0, %1};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%5], {%2, %3};\n\t"
+        "tcgen05.wait::st.sync.aligned;\n\t}"
+        ::"r"(__float_as_uint(a[0])), "r"(__float_as_uint(a[1])), "r"(__float_as_uint(c[0])),
+          "r"(__float_as_uint(c[1])), "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+
 // ------------------------------------------------------------ items
 struct Item {
     int q, s, fb, bt;
@@ -104,10 +152,10 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 
 // Shared-memory layout of the batched kernel: double-buffered TMA stages
 // (peakgram band, vn / weight / c table rows), per-warp track values, the
-// per-thread Kahan sums, stage barriers and arrival counters, and the
+// TMEM address slot, stage barriers and arrival counters, and the
 // toplist bookkeeping.
 struct Layout {
-    int pk[2], vn[2], w[2], c[2], y, cp, ce, sl, acc, comp, tab, bar, done, sel, misc, total;
+    int pk[2], vn[2], w[2], c[2], y, cp, ce, sl, tab, bar, done, tm, sel, misc, total;
 };
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
@@ -134,11 +182,10 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     L.cp = o; o = align128(o + (direct ? 0 : nw * I * wrows * 4));
     L.ce = o; o = align128(o + (direct ? 0 : nw * I * wrows * 8));
     L.sl = o; o = align128(o + SCAP * threads);
-    L.acc = o; o = align128(o + JW * threads * 4);
-    L.comp = o; o = align128(o + JW * threads * 4);
     L.tab = o; o = align128(o + (acc ? nw * 256 * 4 : 0));
     L.bar = o; o = align128(o + 16);
     L.done = o; o = align128(o + 16);
+    L.tm = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
     L.misc = o; o = align128(o + 64);
     L.total = o;
@@ -352,19 +399,29 @@ __device__ void emit_item(const CountArgs& a, const ProbDev& P, const ItemCtx& c
 }
 
 // ------------------------------------------------------------ batched kernel
-// Kahan-compensated fold of the 64-SFT block sums into the per-thread sums
-// kept in shared memory (column `tid`, conflict-free).
-template <int THREADS>
-__device__ __forceinline__ void kahan_fold(float* part, float* sacc, float* scomp, int tid) {
+// This warp's TMEM columns: the CTA's base (read back from shared memory, so that no
+// register holds it through the hot loop), the lanes of the warp's quarter, 64 columns
+// per warp sharing that quarter: [+0, +32) sums, [+32, +64) compensations.
+__device__ __forceinline__ uint32_t tmem_cols(const volatile uint32_t* slot, int warp) {
+    return *slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+}
+
+// Kahan-compensated fold of the 64-SFT block sums into the thread's sums held in TMEM.
+__device__ __forceinline__ void kahan_fold(float* part, uint32_t tacc) {
+    __syncwarp();   // the tcgen05 accesses below are warp-collective
 #pragma unroll
-    for (int j = 0; j < JW; ++j) {
-        const float a0 = sacc[j * THREADS + tid];
-        const float c0 = scomp[j * THREADS + tid];
-        const float y = part[j] - c0;
-        const float t = a0 + y;
-        scomp[j * THREADS + tid] = (t - a0) - y;
-        sacc[j * THREADS + tid] = t;
-        part[j] = 0.f;
+    for (int j0 = 0; j0 < JW; j0 += 2) {
+        float a[2], c[2];
+        tmem_ld2x2(tacc + (uint32_t)j0, a, c);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float y = part[j0 + k] - c[k];
+            const float t = a[k] + y;
+            c[k] = (t - a[k]) - y;
+            a[k] = t;
+            part[j0 + k] = 0.f;
+        }
+        tmem_st2x2(tacc + (uint32_t)j0, a, c);
     }
 }
 
@@ -403,8 +460,6 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     unsigned* done = reinterpret_cast<unsigned*>(smem + L.done);
     SelectSmem& sm = *reinterpret_cast<SelectSmem*>(smem + L.sel);
     TopSmem& ts = *reinterpret_cast<TopSmem*>(smem + L.misc);
-    float* sacc = reinterpret_cast<float*>(smem + L.acc);
-    float* scomp = reinterpret_cast<float*>(smem + L.comp);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int I = a.chunk;
     const int wrows = a.wrows;
@@ -420,6 +475,11 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     int visit = a.cta_visit[blockIdx.x] - 1;
     int region = -1;
 
+    // TMEM for the Kahan sums: 64 columns per warp quarter-slot (256 threads: warps w and
+    // w + 4 share lanes, so 128 columns; 128 threads: 64)
+    constexpr uint32_t TCOLS = THREADS > 128 ? 128u : 64u;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tm);
+    if (warp == 0) tmem_alloc(tslot, TCOLS);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -431,7 +491,9 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         ts.tau = 0ull;
         ts.abort = 0;
     }
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
 
     ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
     if (tid == 0) {
@@ -474,10 +536,13 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
 
         float part[JW];
 #pragma unroll
-        for (int j = 0; j < JW; ++j) {
-            part[j] = 0.f;
-            sacc[j * THREADS + tid] = 0.f;
-            scomp[j * THREADS + tid] = 0.f;
+        for (int j = 0; j < JW; ++j) part[j] = 0.f;
+        {
+            const float z[2] = {0.f, 0.f};
+            const uint32_t tacc = tmem_cols(tslot, warp);
+            __syncwarp();
+#pragma unroll
+            for (int j0 = 0; j0 < JW; j0 += 2) tmem_st2x2(tacc + (uint32_t)j0, z, z);
         }
         uint32_t ones = 0, twos = 0, fours = 0;
         uint32_t e8[NE];   // bit-sliced count of the 'eights' (N < 8 * 2^NE)
@@ -636,7 +701,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     e8[k] ^= eights;
                     eights = t;
                 }
-                if ((g8 & 63) == 56) kahan_fold<THREADS>(part, sacc, scomp, tid);   // every 64 SFTs
+                if ((g8 & 63) == 56) kahan_fold(part, tmem_cols(tslot, warp));   // every 64 SFTs
             }
             if (!LUT) {
                 // the chunk's deferred entries: each lane its own, all lanes at once
@@ -687,19 +752,26 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
             }
         }
         // fold the last partial block and read out the counts
-        kahan_fold<THREADS>(part, sacc, scomp, tid);
+        const uint32_t tacc = tmem_cols(tslot, warp);
+        kahan_fold(part, tacc);
         float nw[JW];
         uint32_t nu[JW];
 #pragma unroll
+        for (int j0 = 0; j0 < JW; j0 += 2) {
+            float sa[2], sc[2];
+            tmem_ld2x2(tacc + (uint32_t)j0, sa, sc);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) nw[j0 + k] = sa[k] - sc[k];
+        }
+#pragma unroll
         for (int j = 0; j < JW; ++j) {
-            nw[j] = sacc[j * THREADS + tid] - scomp[j * THREADS + tid];
             uint32_t cnt = ((ones >> j) & 1u) + 2u * ((twos >> j) & 1u) + 4u * ((fours >> j) & 1u);
 #pragma unroll
             for (int k = 0; k < NE; ++k) cnt += ((e8[k] >> j) & 1u) << (3 + k);
             nu[j] = cnt;
         }
         (void)aborted;
-        if (__syncthreads_or(ts.abort)) return;   // a wait expired somewhere: leave together
+        if (__syncthreads_or(ts.abort)) break;   // a wait expired somewhere: leave together
         emit_item<THREADS>(a, P, cur, b, bvalid, nw, nu, visit, ts, sm);
 
         ++it;
@@ -707,7 +779,12 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         cur = item_ctx(a, decode_item(a, it), THREADS);
         __syncthreads();
     }
-    if (!a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+    if (!ts.abort && !a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+    // every warp is done with its TMEM columns before the allocating warp frees them
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 0) tmem_free(*tslot, TCOLS);
 }
 
 // ------------------------------------------------------------ plain kernel
