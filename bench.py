@@ -215,18 +215,14 @@ def profile_value(name: str, key: str):
     return float(vals[key]), f"profiles/{name}"
 
 
-def profiled_traffic(kind: str, n_sky: int):
-    """DRAM bytes per count launch from the committed ncu summary of this workload. The
-    metric-bank summary is of its 200-sky-point case; every (sky point, f0 block) pass re-reads
-    the orbit table, so its traffic scales with the sky points of the launch."""
+def profiled_traffic(kind: str):
+    """DRAM bytes per count launch from the committed ncu summary of this workload."""
     if kind == "mid":
         return profile_value("count_batched_mid.md", "traffic_bytes_per_launch")
-    if kind in ("metric", "metric-small"):
-        t, src = profile_value("count_batched_metric_small_full.md", "traffic_bytes_per_launch")
-        n0, _ = profile_value("count_batched_metric_small_full.md", "traffic_sky_points")
-        if t is None or not n0:
-            return None, src
-        return t * n_sky / n0, src + (f" (x {n_sky}/{n0:.0f} sky points)" if n_sky != n0 else "")
+    if kind == "metric":
+        return profile_value("count_batched_metric_small_full.md", "traffic_bytes_per_launch")
+    if kind == "metric-small":
+        return profile_value("count_batched_metric_small_full.md", "traffic_bytes_per_launch_small")
     return None, None
 
 
@@ -479,7 +475,7 @@ def main():
     count_rate = pr.n_terms / count_s
     achieved_gbs = count_rate * 4.0 / 1e9
     peak_gbs = n_sm * 128.0 * f_max / 1e9
-    traffic, traffic_src = profiled_traffic(args.workload, pr.S)
+    traffic, traffic_src = profiled_traffic(args.workload)
     roofline = {"bound": "smem", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                 "frac": achieved_gbs / peak_gbs, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "bsh_number_count (track tables + count_batched)",
