@@ -254,6 +254,10 @@ int bsh_plan_direct(const bsh_plan* plan);
 /* Eq. (14)/(15), its significance s_H of Eq. (25), and a fused per-patch    */
 /* toplist of the top_k largest s_H (ties: smaller template id first).       */
 /* Reads the problems' bits, w, sums, v, t and sky arrays.  Capturable.      */
+/* The batched kernels keep their running sums in tensor memory: each CTA    */
+/* takes half a column per thread (at most 256 of an SM's 512 columns) and   */
+/* frees them before it exits; a CTA that starts while other work on its SM  */
+/* holds the columns it needs waits until they are freed.                    */
 /* ------------------------------------------------------------------------ */
 int bsh_number_count(bsh_plan* plan, bsh_stream stream);
 
