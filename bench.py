@@ -186,31 +186,35 @@ class ClockSampler:
         return out
 
 
-def kernel_sha() -> str:
+def code_only(text: str) -> str:
+    """C/CUDA source with comments removed and whitespace runs collapsed."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_sha(root: str = ROOT) -> str:
     """Short hash of the count kernel's sources with comments and whitespace removed, so
     that only code changes invalidate a summary (matches the ncu summaries' stamp)."""
     import hashlib
-    import re
-    src = os.path.join(ROOT, "paper_1904_04873_gb300", "csrc")
+    src = os.path.join(root, "paper_1904_04873_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
-        text = open(os.path.join(src, f), encoding="utf-8").read()
-        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-        text = re.sub(r"//[^\n]*", " ", text)
-        h.update(" ".join(text.split()).encode())
+        h.update(code_only(open(os.path.join(src, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
-def profile_value(name: str, key: str):
+def profile_value(name: str, key: str, root: str = ROOT):
     """A figure recorded in a committed ncu summary, with its source; None when the
     summary is missing or was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", name)
+    path = os.path.join(root, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None, None
     vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith((key + ":", "kernel_source_sha256_16:")))
-    if vals.get("kernel_source_sha256_16", "").strip() != kernel_sha() or key not in vals:
+    if vals.get("kernel_source_sha256_16", "").strip() != kernel_sha(root) or key not in vals:
         return None, f"profiles/{name} (stale: kernel changed since)"
     return float(vals[key]), f"profiles/{name}"
 
