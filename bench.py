@@ -224,9 +224,9 @@ def profiled_traffic(kind: str):
     if kind == "mid":
         return profile_value("count_batched_mid.md", "traffic_bytes_per_launch")
     if kind == "metric":
-        return profile_value("count_batched_metric_small_full.md", "traffic_bytes_per_launch")
+        return profile_value("count_batched_metric_bank.md", "traffic_bytes_per_launch")
     if kind == "metric-small":
-        return profile_value("count_batched_metric_small_full.md", "traffic_bytes_per_launch_small")
+        return profile_value("count_batched_metric_bank.md", "traffic_bytes_per_launch_small")
     return None, None
 
 
@@ -494,7 +494,7 @@ def main():
                                "frac": count_rate / (n_sm * 128.0 * 8.0 * f_max)}
     # the binding ceiling of this kernel is ALU issue: 128 lanes x f_SM per SM, at the thread
     # instructions per term that ncu measured for this kernel variant
-    ipt, ipt_src = profile_value("count_batched_metric_small_full.md" if args.workload.startswith("metric")
+    ipt, ipt_src = profile_value("count_batched_metric_bank.md" if args.workload.startswith("metric")
                                  else "count_batched_small_full.md",
                                  "lut_instr_per_term" if args.track == "lut" else "instr_per_term")
     if ipt:

@@ -50,8 +50,8 @@ def test_committed_summaries_carry_the_current_stamp():
     for name, key in (("count_batched_mid.md", "traffic_bytes_per_launch"),
                       ("count_batched_small_full.md", "instr_per_term"),
                       ("count_batched_small_full.md", "lut_instr_per_term"),
-                      ("count_batched_metric_small_full.md", "instr_per_term"),
-                      ("count_batched_metric_small_full.md", "traffic_bytes_per_launch")):
+                      ("count_batched_metric_bank.md", "instr_per_term"),
+                      ("count_batched_metric_bank.md", "traffic_bytes_per_launch")):
         v, src = bench.profile_value(name, key)
         assert v is not None and v > 0, (name, key, src)
 
