@@ -248,6 +248,18 @@ int bsh_plan_accumulate(const bsh_plan* plan);
 int bsh_plan_set_direct(bsh_plan* plan, int mode);
 int bsh_plan_direct(const bsh_plan* plan);
 
+/* Bounded waits of the batched count.  Each CTA stages SFT chunks through two
+ * buffers and waits on a barrier per stage; a wait polls at most `polls` times
+ * (0 = the default, 2^22 polls: about a second or more) and then gives up: the
+ * CTA waits, with the same bound, for the copies it still has in flight, frees
+ * its tensor memory and exits, and bsh_sync_status returns BSH_ERR_TIMEOUT.
+ * skip_stage is a test hook for that path: >= 0 makes every CTA leave the copies
+ * of its skip_stage-th stage (0 = its first) unissued, so that the wait on them
+ * expires without any fault; -1 (the default) issues every stage.  Drops a
+ * recorded graph; not capturable.  The paper has no counterpart: this is the
+ * library's own failure detection. */
+int bsh_plan_set_wait(bsh_plan* plan, int polls, int skip_stage);
+
 /* ------------------------------------------------------------------------ */
 /* (iii) Number count, Sec. IV.C and V.A: for every template the weighted    */
 /* sum n = sum_i w_i * bit_i[k_i] along the track k_i = round(f(t_i) T_c) of  */
@@ -471,11 +483,13 @@ int bsh_template_bank(const bsh_bank_spec* spec, int* n_orbit, double* orbit, in
 /*   template ids ((s * B + b) * n_f0 + j).  power, s_p [n] DEVICE float:     */
 /*   P and s_P of Eq. (26) for each id, the same values bsh_power_sum gives. */
 /* Returns BSH_ERR_WORKSPACE when the problem's tables exceed the static     */
-/* array (S * N' * 8 + n_Om * n_T * N' * 12 bytes plus the grids, with N'   */
-/* = N rounded up to 256).  The first call on a device looks up the array's */
-/* device address (make that first call before any stream capture).  Every  */
-/* call overwrites the whole array, so calls that overlap on the GPU (other */
-/* streams, other threads) race and must be serialised by the caller.       */
+/* array: S * N' * 8 + R * N' * 12 + B * 16 bytes plus the grids, with N' = */
+/* N rounded up to 256, R the orbit rows (n_Om * n_T * max(1, n_kappa) *    */
+/* max(1, n_eta) for a grid, n_orbit for a bank) and B the binary templates.*/
+/* The first call on a device looks up the array's device address (make    */
+/* that first call before any stream capture).  Every call overwrites the   */
+/* whole array, so calls that overlap on the GPU (other streams, other      */
+/* threads) race and must be serialised by the caller.                      */
 /* Kernel-side errors are reported by bsh_sync_status.                      */
 /* ------------------------------------------------------------------------ */
 #define BSH_STATIC_SCRATCH_BYTES (32u << 20)

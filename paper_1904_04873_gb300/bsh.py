@@ -132,6 +132,7 @@ _SIGS = {
     "bsh_binary_resolution": (ctypes.c_int, [ctypes.c_double] * 8 + [ctypes.c_void_p] * 3),
     "bsh_plan_set_direct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bsh_plan_direct": (ctypes.c_int, [ctypes.c_void_p]),
+    "bsh_plan_set_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "bsh_cand_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -375,6 +376,11 @@ class Plan:
         """bsh_plan_set_direct: -1 automatic, 0 per-warp C values, 1 per-term C values."""
         _check(lib().bsh_plan_set_direct(self.h, mode), "bsh_plan_set_direct")
         return lib().bsh_plan_direct(self.h)
+
+    def set_wait(self, polls: int = 0, skip_stage: int = -1):
+        """bsh_plan_set_wait: the staging-barrier poll limit (0 = default) and the test hook
+        that leaves one stage per CTA unissued (-1 = none)."""
+        _check(lib().bsh_plan_set_wait(self.h, polls, skip_stage), "bsh_plan_set_wait")
 
     def autotune(self, stream=None):
         _check(lib().bsh_autotune(self.h, _stream(stream)), "bsh_autotune")

@@ -281,6 +281,66 @@ __host__ __device__ uint32_t fp_window_slow(int v0, int v1, int pbase, int pos_m
     return fp_window_exact(v0, v1, pbase, pos_max, s, M, row, exact_o, bad);
 }
 
+#ifdef __CUDACC__
+// Stage 2, Eq. (26), for one template (s, b, j): P = sum_i w_i rho_i[k_i] along its exact
+// track, one warp with lanes over SFTs.  The bin of each term is the fixed-point track's,
+// or the FP64 expression within the margin M of a rounding boundary.  FP32 weights: a
+// Kahan-compensated FP32 sum per lane, then a shuffle tree; FP64 weights (the plain form):
+// FP64 sums.  Every lane returns the total.  A bin outside the loaded band records ST_RANGE
+// and its term is skipped.
+__device__ __forceinline__ double warp_power_sum(const ProbDev& P, int s, int b, int j, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    const double F = P.F0 + (double)j;
+    const int F2 = (int)llrint(2.0 * F);
+    const int G = P.G0 + j;
+    const int ot = P.brow[b];
+    const int apq = P.bapq[b];
+    const double ap = P.bap[b];
+    const int s_y = P.fp.s_y, M = P.fp.M;
+    const int cell = 1 << s_y;
+    const bool plain = P.w64 != nullptr && P.w32 == nullptr;
+    const double* n = P.sky + 3 * (size_t)s;
+    float sum = 0.f, comp = 0.f;
+    double sum64 = 0.0;
+    for (int i = lane; i < P.N; i += 32) {
+        const int Z = make_Z(F2, P.vn_q[(size_t)s * P.Np + i], P.fp);
+        const int C = make_C(F2, P.c_q[(size_t)ot * P.Np + i], P.fp);
+        const int v = Z - mulhi32(apq, C);
+        const int fr = v & (cell - 1);
+        int o = v >> s_y;
+        if (fr < M || fr > cell - M) {
+            const double* vv = P.v + 3 * (size_t)i;
+            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(vv[0], n[0]), __dmul_rn(vv[1], n[1])),
+                                        __dmul_rn(vv[2], n[2]));
+            const double D = __dsub_rn(vn, __dmul_rn(ap, P.c64[(size_t)ot * P.Np + i]));
+            const double x = __dadd_rn(F, __dmul_rn(F, D));
+            o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)G);
+        }
+        const int col = G + o - P.k_lo;
+        if (col < 0 || col >= P.K) {
+            set_status(status, ST_RANGE);
+            continue;
+        }
+        const float rho = __ldg(P.rho + (size_t)i * P.K + col);
+        if (plain) {
+            sum64 = __dadd_rn(sum64, __dmul_rn(P.w64[(size_t)s * P.Np + i], (double)rho));
+        } else {
+            const float x = P.w32[(size_t)s * P.Np + i] * rho;
+            const float y = x - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+    }
+    if (plain) {
+        for (int o = 16; o > 0; o >>= 1) sum64 += __shfl_xor_sync(0xffffffffu, sum64, o);
+        return sum64;
+    }
+    float v = sum - comp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return (double)v;
+}
+#endif
 
 // Raises a kernel's dynamic shared-memory limit once (never inside a graph
 // capture once the first eager launch has set it).
@@ -315,6 +375,8 @@ struct CountArgs {
     int acc_mode;                // weighted accumulation variant of the batched kernel
     int lut;                     // 1: look-up-table approximation of the track (BSH_MODE_LUT)
     int direct;                  // 1: C_q formed per term from the staged rows (predicated-add only)
+    int wait_polls;              // polls of a staging barrier before a wait gives up (BSH_ERR_TIMEOUT)
+    int skip_stage;              // test hook: per-CTA stage sequence number left unissued (-1: none)
 };
 
 // TMA descriptors of the batched kernel, one pair per problem: the peakgram rows and

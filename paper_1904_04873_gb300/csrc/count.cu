@@ -66,9 +66,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Bounded wait on an mbarrier phase: false after ~2^22 polls (seconds).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+// Bounded wait on an mbarrier phase: false after `limit` polls (2^22 by default: seconds).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 32) __nanosleep(64);
     }
@@ -233,9 +233,24 @@ __device__ __forceinline__ ItemCtx item_ctx(const CountArgs& a, const Item& it, 
     return c;
 }
 
-// Issues the TMA / bulk copies of chunk `ch` of item `c` into buffer `buf`.
+// Sequence number of the stage whose copies are in flight into buffer b, or -1: entries
+// 2 and 3 of the `done` words.
+__device__ __forceinline__ int* inflight_slots(unsigned char* smem, const Layout& L) {
+    return reinterpret_cast<int*>(smem + L.done) + 2;
+}
+
+// Issues the TMA / bulk copies of chunk `ch` of item `c` into buffer `buf`; `seq` is the
+// stage's sequence number within the CTA.  The stage numbered a.skip_stage (a test hook,
+// normally -1) is left unissued: nothing completes its barrier phase, so the wait on it
+// expires.
 __device__ __forceinline__ void issue_stage(const CountArgs& a, const TmapSet& maps, const ItemCtx& c, int ch,
-                                            unsigned char* smem, const Layout& L, int buf) {
+                                            unsigned char* smem, const Layout& L, int buf, int seq) {
+    int* inflight = inflight_slots(smem, L);
+    if (seq == a.skip_stage) {
+        inflight[buf] = -1;
+        return;
+    }
+    inflight[buf] = seq;
     const ProbDev& P = a.probs[c.q];
     const int I = a.chunk;
     const int i0 = ch * I;
@@ -486,6 +501,8 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         fence_mbar_init();
         done[0] = 0u;
         done[1] = 0u;
+        inflight_slots(smem, L)[0] = -1;
+        inflight_slots(smem, L)[1] = -1;
         ts.count = 0;
         ts.have_tau = 0;
         ts.tau = 0ull;
@@ -497,10 +514,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
 
     ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
     if (tid == 0) {
-        issue_stage(a, maps, cur, 0, smem, L, 0);
+        issue_stage(a, maps, cur, 0, smem, L, 0, 0);
         ItemCtx nx;
         int nch;
-        if (advance_chunk(a, it, 0, 1, it_end, THREADS, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1);
+        if (advance_chunk(a, it, 0, 1, it_end, THREADS, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1, 1);
     }
     unsigned g = 0;   // chunk sequence number within this CTA
 
@@ -555,7 +572,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         bool aborted = false;
         for (int ch = 0; ch < cur.nchunks; ++ch, ++g) {
             const int buf = g & 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars[buf], (g >> 1) & 1))) {   // warp-uniform exit
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars[buf], (g >> 1) & 1, a.wait_polls))) {   // warp-uniform exit
                 if (lane == 0) {
                     set_status(a.status, ST_TIMEOUT);
                     ts.abort = 1;
@@ -747,7 +764,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                     ItemCtx nx;
                     int nch;
                     if (advance_chunk(a, it, ch, 2, it_end, THREADS, &nx, &nch))
-                        issue_stage(a, maps, nx, nch, smem, L, buf);
+                        issue_stage(a, maps, nx, nch, smem, L, buf, (int)g + 2);
                 }
             }
         }
@@ -780,6 +797,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         __syncthreads();
     }
     if (!ts.abort && !a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+    // after an expired wait, copies issued into the other buffer may still be landing in this
+    // CTA's shared memory: wait (bounded) for every stage still marked in flight before the
+    // CTA exits (every warp is past its last issue: they all met at the exit barrier)
+    if (ts.abort && tid == 0) {
+        const int* inflight = inflight_slots(smem, L);
+        for (int bb = 0; bb < 2; ++bb)
+            if (inflight[bb] >= 0) (void)mbar_wait(&bars[bb], ((unsigned)inflight[bb] >> 1) & 1u, a.wait_polls);
+    }
     // every warp is done with its TMEM columns before the allocating warp frees them
     tmem_fence_before();
     __syncthreads();

@@ -156,6 +156,8 @@ void binary_bounds(const ProbHost& h, double* ap_max, double* c_max) {
 
 }  // namespace
 
+constexpr int kDefaultWaitPolls = 1 << 22;   // about a second or more of polling
+
 struct bsh_plan {
     int n = 0;
     std::vector<ProbHost> P;
@@ -172,6 +174,8 @@ struct bsh_plan {
     int direct = 0;                        // the choice in effect
     int direct_tuned = -1;                 // the autotuner's choice under direct_opt = -1 (-1: none yet)
     int one_cta = 0;                       // 1: one CTA per SM with the unshrunk stage (autotuned)
+    int wait_polls = kDefaultWaitPolls;    // staging-barrier polls before a wait gives up
+    int skip_stage = -1;                   // test hook: stage left unissued in every CTA (-1: none)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
@@ -736,6 +740,8 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.acc_mode = p->acc_mode;
     a.direct = p->direct;
     a.lut = p->lut;
+    a.wait_polls = p->wait_polls;
+    a.skip_stage = p->skip_stage;
     a.max_n = 0;
     for (auto& h : p->P) a.max_n = std::max(a.max_n, h.d.N);
     return a;
@@ -979,6 +985,13 @@ int bsh_plan_set_direct(bsh_plan* p, int mode) {
 }
 
 int bsh_plan_direct(const bsh_plan* p) { return p ? p->direct : -1; }
+
+int bsh_plan_set_wait(bsh_plan* p, int polls, int skip_stage) {
+    if (!p || polls < 0 || skip_stage < -1) return BSH_ERR_ARG;
+    p->wait_polls = polls ? polls : kDefaultWaitPolls;
+    p->skip_stage = skip_stage;
+    return bsh_graph_reset(p);
+}
 
 int bsh_track_precision(bsh_plan* p, int problem, int s_begin, int s_end, unsigned long long* counts,
                         bsh_stream stream) {
@@ -1298,7 +1311,7 @@ __global__ void static_bapq(const ProbDev* probs) {
         const_cast<int32_t*>(P.bapq)[b] = (int32_t)llrint(P.bap[b] * sc);
 }
 
-// One warp per listed template: Eq. (26) along the track, as in the plan's power kernel.
+// One warp per listed template: Eq. (26) along the track (the plan's power kernel's sum).
 __global__ void power_list_kernel(const ProbDev* probs, const int64_t* ids, int n, float* power, float* s_p,
                                   unsigned* status) {
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1319,47 +1332,11 @@ __global__ void power_list_kernel(const ProbDev* probs, const int64_t* ids, int 
     const long long rem = id % per_s;
     const int b = (int)(rem / P.n_f0);
     const int j = (int)(rem % P.n_f0);
-    const double F = P.F0 + (double)j;
-    const int F2 = (int)llrint(2.0 * F);
-    const int G = P.G0 + j;
-    const int ot = P.brow[b];
-    const int apq = P.bapq[b];
-    const double ap = P.bap[b];
-    const int s_y = P.fp.s_y, M = P.fp.M;
-    const int cell = 1 << s_y;
-    const double* nv = P.sky + 3 * (size_t)s;
-    float sum = 0.f, comp = 0.f;
-    for (int i = lane; i < P.N; i += 32) {
-        const int Z = make_Z(F2, P.vn_q[(size_t)s * P.Np + i], P.fp);
-        const int C = make_C(F2, P.c_q[(size_t)ot * P.Np + i], P.fp);
-        const int v = Z - mulhi32(apq, C);
-        const int fr = v & (cell - 1);
-        int o = v >> s_y;
-        if (fr < M || fr > cell - M) {
-            const double* vv = P.v + 3 * (size_t)i;
-            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(vv[0], nv[0]), __dmul_rn(vv[1], nv[1])),
-                                        __dmul_rn(vv[2], nv[2]));
-            const double D = __dsub_rn(vn, __dmul_rn(ap, P.c64[(size_t)ot * P.Np + i]));
-            const double x = __dadd_rn(F, __dmul_rn(F, D));
-            o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)G);
-        }
-        const int col = G + o - P.k_lo;
-        if (col < 0 || col >= P.K) {
-            set_status(status, ST_RANGE);
-            continue;
-        }
-        const float x = P.w32[(size_t)s * P.Np + i] * __ldg(P.rho + (size_t)i * P.K + col);
-        const float y = x - comp;
-        const float t = sum + y;
-        comp = (t - sum) - y;
-        sum = t;
-    }
-    float v = sum - comp;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const double v = warp_power_sum(P, s, b, j, status);
     if (lane == 0) {
         const double sw = P.sum_w[s], sw2 = P.sum_w2[s];
-        power[e] = v;
-        s_p[e] = sw2 > 0.0 ? (float)(((double)v - sw) / sqrt(sw2)) : 0.f;
+        power[e] = (float)v;
+        s_p[e] = sw2 > 0.0 ? (float)((v - sw) / sqrt(sw2)) : 0.f;
     }
 }
 

@@ -26,57 +26,7 @@ __global__ void __launch_bounds__(PW * 32) power_kernel(const PowerArgs a) {
     const long long rem = id % per_s;
     const int b = (int)(rem / P.n_f0);
     const int j = (int)(rem % P.n_f0);
-    const double F = P.F0 + (double)j;
-    const int F2 = (int)llrint(2.0 * F);
-    const int G = P.G0 + j;
-    const int ot = P.brow[b];
-    const int apq = P.bapq[b];
-    const double ap = P.bap[b];
-    const int s_y = P.fp.s_y, M = P.fp.M;
-    const int cell = 1 << s_y;
-    const bool plain = P.w64 != nullptr && P.w32 == nullptr;
-    const double* n = P.sky + 3 * (size_t)s;
-    float sum = 0.f, comp = 0.f;
-    double sum64 = 0.0;
-    for (int i = lane; i < P.N; i += 32) {
-        const int Z = make_Z(F2, P.vn_q[(size_t)s * P.Np + i], P.fp);
-        const int C = make_C(F2, P.c_q[(size_t)ot * P.Np + i], P.fp);
-        const int v = Z - mulhi32(apq, C);
-        const int fr = v & (cell - 1);
-        int o = v >> s_y;
-        if (fr < M || fr > cell - M) {
-            const double* vv = P.v + 3 * (size_t)i;
-            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(vv[0], n[0]), __dmul_rn(vv[1], n[1])),
-                                        __dmul_rn(vv[2], n[2]));
-            const double D = __dsub_rn(vn, __dmul_rn(ap, P.c64[(size_t)ot * P.Np + i]));
-            const double x = __dadd_rn(F, __dmul_rn(F, D));
-            o = (int)((long long)floor(__dadd_rn(x, 0.5)) - (long long)G);
-        }
-        const int col = G + o - P.k_lo;
-        if (col < 0 || col >= P.K) {
-            set_status(a.status, ST_RANGE);
-            continue;
-        }
-        const float rho = __ldg(P.rho + (size_t)i * P.K + col);
-        if (plain) {
-            sum64 = __dadd_rn(sum64, __dmul_rn(P.w64[(size_t)s * P.Np + i], (double)rho));
-        } else {
-            const float x = P.w32[(size_t)s * P.Np + i] * rho;
-            const float y = x - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
-        }
-    }
-    double tot;
-    if (plain) {
-        for (int o = 16; o > 0; o >>= 1) sum64 += __shfl_xor_sync(0xffffffffu, sum64, o);
-        tot = sum64;
-    } else {
-        float v = sum - comp;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        tot = (double)v;
-    }
+    const double tot = warp_power_sum(P, s, b, j, a.status);
     if (lane == 0) {
         const double sw = P.sum_w[s], sw2 = P.sum_w2[s];
         c->power = (float)tot;

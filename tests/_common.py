@@ -84,3 +84,41 @@ def inject_on_track(pr, rho, s, b, j, excess=3.0):
 
 
 P_TH = math.exp(-1.6)
+
+
+def _dense_shard(args):
+    """Spawned process: the oracle's dense counts of the s-th listed sky point for the binary
+    templates of one Omega of a circular grid (contiguous b = iOm * n_T * n_ap + b')."""
+    import oracle as _orc
+    kw, s, iOm = args
+    sub = dict(kw)
+    sub["sky"] = kw["sky"][s:s + 1]
+    sub["w"] = kw["w"][s:s + 1]
+    sub["Omega"] = kw["Omega"][iOm:iOm + 1]
+    sub["T_asc"] = kw["T_asc"][iOm:iOm + 1]
+    return s, iOm, _orc.OracleProblem(**sub).count_dense()
+
+
+def oracle_dense_parallel(pr, bits, w, sky_points, procs=0):
+    """The oracle's dense counts ([len(sky_points), B, n_f0] per field, as count_dense) of
+    a circular-grid problem, computed in spawned processes, one (sky point, Omega) shard each.
+    The arithmetic is the oracle's count_one, unchanged; only the work is split."""
+    import multiprocessing as mp
+    import os
+    assert pr.kappa is None and pr.eta is None and pr.orbit is None
+    sel = np.asarray(sky_points, dtype=np.int64)
+    kw = dict(bits=bits, w=np.ascontiguousarray(w[sel]), v=pr.v, t=pr.t, F0=pr.F0, n_f0=pr.n_f0,
+              sky=np.ascontiguousarray(pr.sky[sel]), a_p=pr.a_p, Omega=pr.Omega, T_asc=pr.T_asc, k_lo=pr.k_lo,
+              K=pr.K, rho_th=pr.rho_th)
+    n_Om = pr.Omega.size
+    per_Om = pr.B // n_Om
+    shape = (len(sky_points), pr.B, pr.n_f0)
+    out = dict(n_unw=np.empty(shape, np.int32), n_w=np.empty(shape), n_tie=np.empty(shape, np.int32),
+               unw_lo=np.empty(shape, np.int32), unw_hi=np.empty(shape, np.int32),
+               w_lo=np.empty(shape), w_hi=np.empty(shape))
+    tasks = [(kw, s, k) for s in range(sel.size) for k in range(n_Om)]
+    with mp.get_context("spawn").Pool(procs or os.cpu_count() or 1) as pool:
+        for s, iOm, d in pool.imap_unordered(_dense_shard, tasks):
+            for f, a in d.items():
+                out[f][s, iOm * per_Om:(iOm + 1) * per_Om] = a[0]
+    return out

@@ -88,6 +88,19 @@ def test_valid_plan_and_workspace(small):
     L.bsh_plan_destroy(h)
 
 
+def test_wait_limit_arguments(small):
+    fp = FakeProblem(small)
+    rc, h = create([fp.d])
+    assert rc == bsh.OK
+    L = bsh.lib()
+    assert L.bsh_plan_set_wait(h, -1, -1) == bsh.ERR_ARG
+    assert L.bsh_plan_set_wait(h, 0, -2) == bsh.ERR_ARG
+    assert L.bsh_plan_set_wait(h, 4096, 1) == bsh.OK
+    assert L.bsh_plan_set_wait(h, 0, -1) == bsh.OK
+    assert L.bsh_plan_set_wait(None, 0, -1) == bsh.ERR_ARG
+    L.bsh_plan_destroy(h)
+
+
 def test_plain_plan(small):
     fp = FakeProblem(small)
     rc, h = create([fp.d], mode=bsh.MODE_PLAIN)

@@ -53,6 +53,38 @@ def test_resolution_scalings(res):
         math.sqrt(6.0 * 72.0 * 6.0) / math.pi ** 3, rel=1e-13)
 
 
+def _golden_points():
+    """Rows of tests/golden/bank_resolution.txt: (inputs, expected spacings), the expected values
+    evaluated from the closed forms written there."""
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bank_resolution.txt")
+    env = {"pi": math.pi, "sqrt": math.sqrt, "__builtins__": {}}
+    rows = []
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        lhs, rhs = line.split("|")
+        name, *vals = lhs.split()
+        f, T_c, T_obs, a, Om = (float(x) for x in vals[:5])
+        m = [float(Fraction(x)) for x in vals[5:8]]
+        exp = [eval(x, env) for x in rhs.split()]
+        rows.append((name, (f, T_c, T_obs, a, Om, *m), exp))
+    return rows
+
+
+@pytest.mark.parametrize("res", ["oracle", "library"])
+def test_resolution_hand_worked_points(res):
+    # each spacing separately, at points worked by hand (tests/golden/bank_resolution.txt)
+    fn = obank.resolution if res == "oracle" else bsh.binary_resolution
+    rows = _golden_points()
+    assert [r[0] for r in rows] == ["A", "B"]
+    for name, args, exp in rows:
+        got = fn(*args)
+        for k, (g, e) in enumerate(zip(got, exp)):
+            assert g == pytest.approx(e, rel=1e-13), (name, ("d_ap", "d_Om", "d_t")[k], g, e)
+
+
 def test_bank_layout_and_spacings():
     sp = spec(ap_block=1.5)
     orbit, bo, ba = obank.template_bank(**sp)

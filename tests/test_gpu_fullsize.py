@@ -1,20 +1,26 @@
-"""Full-size sampled parity on the benchmark workload (mid: 2 x 2000 SFTs,
-2000 sky points in 40 patches, 32^3 binary templates, 90 f0 bins, top-1000),
-in the launch configuration bench.py times (autotuned batched plan), and on the
-shapes of the other workloads (full scale with stage 2, multi-band batching,
-the eccentric grid, a metric template bank).
+"""Full-size parity on the benchmark workload (mid: 2 x 2000 SFTs, 2000 sky
+points in 40 patches, 32^3 binary templates, 90 f0 bins, top-1000), in the
+launch configuration bench.py times (autotuned batched plan), end to end (the
+GPU forms the peakgram and the weights itself; they must equal the oracle's),
+and on the shapes of the other workloads (full scale with stage 2, multi-band
+batching, the eccentric grid, a metric template bank).
 
-The oracle cannot count 5.9e9 templates, so it recomputes sampled outputs
-one template at a time: toplist entries (counts, s_H, P), and random
-templates outside the lists, whose oracle s_H must not exceed the list's
-k-th score (the toplist property).
+The oracle cannot count all 5.9e9 templates.  It counts two whole sky points
+densely (2 x 32768 x 90 templates over all 4000 SFTs, in spawned processes),
+compared element by element with the kernel's dense counts in the same tile
+shape, and their toplist with the oracle's full sort; and it recomputes
+sampled outputs of the full run one template at a time: toplist entries
+(counts, s_H, P), random templates outside the lists, whose oracle s_H must
+not exceed the list's k-th score (the toplist property), and, for the two
+densely counted sky points, every template of theirs above that k-th score.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_1904_04873_gb300 import bsh, synth
-from gpu_common import REL_TOL, device_problem
+from _common import oracle_dense_parallel
+from gpu_common import REL_TOL, check_dense, check_toplists, device_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -29,16 +35,85 @@ def run():
     build.build()
     torch.cuda.set_device(0)
     pr = synth.mid()
-    dp, op, wq = device_problem(pr, "f16")
+    # end to end: the GPU forms the peakgram, rho and fp16 weights from the raw inputs
+    dp, op, wq = device_problem(pr, "f16", oracle_fed=False)
+    assert bsh.sync_status() == bsh.OK
+    assert np.array_equal(dp.bits.cpu().numpy().view(np.uint32), op.bits)
+    assert np.array_equal(dp.rho.cpu().numpy(), op.rho)
+    assert np.array_equal(dp.w.double().cpu().numpy(), wq)
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
-    plan.autotune()
+    tile = plan.autotune()
     plan.number_count()
     cands, n = plan.toplist()
     plan.power_sum(100)
     assert bsh.sync_status() == bsh.OK
     lists = bsh.cands_to_numpy(cands, n)
     plan.close()
-    return pr, op, wq, lists
+    return pr, op, wq, lists, tile
+
+
+DENSE_SKY = [0, 1]
+
+
+@pytest.fixture(scope="module")
+def dense(run):
+    """The oracle's dense counts of sky points 0 and 1 at full size, with their s_H."""
+    pr, op, wq, _, _ = run
+    d = oracle_dense_parallel(pr, op.bits, wq, DENSE_SKY)
+    sw = wq[DENSE_SKY].sum(axis=1)
+    sw2 = (wq[DENSE_SKY] ** 2).sum(axis=1)
+    p = np.exp(-pr.rho_th)
+    sc = (d["n_w"] - p * sw[:, None, None]) / np.sqrt(p * (1 - p) * sw2)[:, None, None]
+    return d, sc
+
+
+def test_dense_slice_full_size(run, dense):
+    # sky points 0 and 1 at the full B x F x N of the bench workload, searched as one patch by
+    # a plan in the bench's tile shape; every count against the oracle, then the patch's
+    # toplist against the oracle's full sort of all 5.9e6 scores
+    pr, op, wq, _, tile = run
+    d, sc = dense
+    sub = synth.mid(sky=pr.sky[DENSE_SKY], patch_size=len(DENSE_SKY))
+    dp = bsh.DeviceProblem(sub, w_dtype="f16")
+    dp.prepare()
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=tile["threads"], sft_chunk=tile["sft_chunk"])
+    plan.set_direct(tile["direct"])
+    plan.set_accumulate(tile["accumulate"])
+    t = plan.tile()
+    assert (t["threads"], t["sft_chunk"], t["direct"], t["accumulate"]) == \
+        (tile["threads"], tile["sft_chunk"], tile["direct"], tile["accumulate"])
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    check_dense(gu[0], gw[0], d)
+    plan.number_count()
+    check_toplists(plan, dp, 0, [sc], pr.top_k, 2e-4)
+    assert bsh.sync_status() == bsh.OK
+    plan.close()
+
+
+def test_full_run_toplist_complete_on_dense_sky_points(run, dense):
+    # patch 0 of the full run holds sky points 0-49: every template of sky points 0 and 1 whose
+    # oracle s_H clears the list's k-th score by the score tolerance is in the list, and every
+    # list entry of theirs has the oracle's counts
+    pr, op, wq, lists, _ = run
+    d, sc = dense
+    g = lists[0]
+    kth = float(g["s_h"][-1])
+    per_s = pr.B * pr.n_f0
+    in_list = {int(x) for x in g["template_id"]}
+    for k, s in enumerate(DENSE_SKY):
+        above = np.flatnonzero(sc[k].ravel() > kth + 2e-4)
+        missing = [int(x) for x in above if s * per_s + int(x) not in in_list]
+        assert not missing, (s, missing[:5])
+    for c in g:
+        s, rem = divmod(int(c["template_id"]), per_s)
+        if s not in DENSE_SKY:
+            continue
+        k = DENSE_SKY.index(s)
+        b, j = divmod(rem, pr.n_f0)
+        assert d["unw_lo"][k, b, j] <= int(c["n_unw"]) <= d["unw_hi"][k, b, j]
+        assert abs(float(c["n_w"]) - d["n_w"][k, b, j]) <= REL_TOL * d["n_w"][k, b, j]
+        assert abs(float(c["s_h"]) - sc[k, b, j]) < 2e-4
 
 
 def _score(op, wq, s, b, j):
@@ -48,7 +123,7 @@ def _score(op, wq, s, b, j):
 
 
 def test_sampled_toplist_entries(run):
-    pr, op, wq, lists = run
+    pr, op, wq, lists, _ = run
     rng = np.random.default_rng(8)
     per_s = pr.B * pr.n_f0
     patches = [0, len(lists) - 1] + list(rng.choice(len(lists), 2, replace=False))
@@ -73,7 +148,7 @@ def test_sampled_toplist_entries(run):
 
 
 def test_random_templates_respect_the_kth_score(run):
-    pr, op, wq, lists = run
+    pr, op, wq, lists, _ = run
     rng = np.random.default_rng(9)
     per_s = pr.B * pr.n_f0
     for p in rng.choice(len(lists), 3, replace=False):

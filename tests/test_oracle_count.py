@@ -15,8 +15,8 @@ import pytest
 
 import oracle
 from paper_1904_04873_gb300 import synth
-from _common import (P_TH, inject_on_track, oracle_inputs, oracle_problem, pack_bits, small_mid,
-                     template_of, track_bins)
+from _common import (P_TH, inject_on_track, oracle_dense_parallel, oracle_inputs, oracle_problem, pack_bits,
+                     small_mid, template_of, track_bins)
 
 
 @pytest.fixture(scope="module")
@@ -166,3 +166,16 @@ def test_power_sum_closed_forms(prob):
     p12 = oracle_problem(pr, bits, w, rho=r1 + r2).power_sum(s, b, j)
     assert abs(p1 + p2 - p12) < 1e-7 * p12   # r1 + r2 is rounded to float32
     assert abs(oracle.power_significance(w[s].sum(), w[s].sum(), (w[s] ** 2).sum())) < 1e-15
+
+
+def test_parallel_dense_equals_the_oracle_dense():
+    # the process-sharded dense count used by the full-size GPU test splits only the work
+    pr = small_mid(n_sky=5, n_per_det=40, n_ap=3, n_P=4, n_T=2)
+    rho, bits, w = oracle_inputs(pr, "f16")
+    ref = oracle_problem(pr, bits, w).count_dense(1, 5)
+    got = oracle_dense_parallel(pr, bits, w, [1, 2, 3, 4], procs=2)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    got = oracle_dense_parallel(pr, bits, w, [3], procs=2)
+    for k in ref:
+        assert np.array_equal(got[k][0], ref[k][2]), k

@@ -1,16 +1,17 @@
-"""bsh_power_sum_static against bsh_power_sum, through the C ABI.
+"""bsh_power_sum_static against bsh_power_sum and the oracle, through the C ABI.
 
 bsh_power_sum_static is for callers that cannot allocate device memory (no
 cudaMalloc and no caching allocator available where they run): it needs no
 plan and no workspace and keeps its track tables in a fixed-size static
 device array inside the library.  Its P and s_P must match the plan-based
-power sum of the same candidates within the stage-2 tolerance, on two calls
-in a row (the second call reuses, and must fully rewrite, the static array).
-This file is collected last on purpose.
+power sum of the same candidates, and the FP64 oracle's Eq. (26) sums, within
+the stage-2 tolerance, on two calls in a row (the second call reuses, and must
+fully rewrite, the static array).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1904_04873_gb300 import bsh
 from _common import small_mid
 from gpu_common import REL_TOL, device_problem
@@ -40,27 +41,38 @@ def _reference(dp, top_k):
     return np.concatenate(lists)
 
 
-def _check(dp, ref):
+def _check(dp, ref, op, wq):
     ids = torch.as_tensor(ref["template_id"], dtype=torch.int64, device="cuda")
     power, s_p = bsh.power_sum_static(dp, ids)
     assert bsh.sync_status() == bsh.OK
     power = power.cpu().numpy()
     s_p = s_p.cpu().numpy()
+    # against the plan's bsh_power_sum of the same templates
     P = ref["power"].astype(np.float64)
     assert np.all(np.abs(power - P) <= REL_TOL * np.abs(P))
     assert np.all(np.abs(s_p - ref["s_p"]) < 1e-4)
+    # against the oracle's FP64 sums (Eq. (26)) along the exact track
+    pr = dp.pr
+    per_s = pr.B * pr.n_f0
+    for e, tid in enumerate(ref["template_id"]):
+        s, rem = divmod(int(tid), per_s)
+        b, j = divmod(rem, pr.n_f0)
+        Po = op.power_sum(s, b, j)
+        assert abs(float(power[e]) - Po) <= REL_TOL * Po
+        sPo = oracle.power_significance(Po, wq[s].sum(), (wq[s] ** 2).sum())
+        assert abs(float(s_p[e]) - sPo) < 1e-4
 
 
 def test_static_power_sum_matches_plan_twice():
     pr1 = small_mid(n_sky=6, n_per_det=150, n_ap=4, n_P=3, n_T=3, patch_size=3, top_k=30)
     pr2 = small_mid(n_sky=9, n_per_det=100, n_ap=8, n_P=2, n_T=4, patch_size=3, top_k=20, seed=77)
-    dp1, _, _ = device_problem(pr1, "f16")
-    dp2, _, _ = device_problem(pr2, "f32")
+    dp1, op1, wq1 = device_problem(pr1, "f16")
+    dp2, op2, wq2 = device_problem(pr2, "f32")
     ref1 = _reference(dp1, 30)
     ref2 = _reference(dp2, 20)
-    _check(dp1, ref1)      # first call on this device sets up the static scratch
-    _check(dp2, ref2)      # second call, different problem: the array is rewritten
-    _check(dp1, ref1)
+    _check(dp1, ref1, op1, wq1)      # first call on this device sets up the static scratch
+    _check(dp2, ref2, op2, wq2)      # second call, different problem: the array is rewritten
+    _check(dp1, ref1, op1, wq1)
 
 
 def test_static_power_sum_eccentric_grid():
@@ -68,18 +80,18 @@ def test_static_power_sum_eccentric_grid():
     from paper_1904_04873_gb300 import synth
     pr = synth.eccentric(n_sky=6, n_per_det=150, n_ap=4, n_P=2, n_T=2, n_kap=3, n_eta=2, e_max=0.05,
                          patch_size=3, top_k=25)
-    dp, _, _ = device_problem(pr, "f16")
+    dp, op, wq = device_problem(pr, "f16")
     ref = _reference(dp, 25)
-    _check(dp, ref)
+    _check(dp, ref, op, wq)
 
 
 def test_static_power_sum_explicit_bank():
     # an explicit (metric) bank is staged in the static array as given
     from test_gpu_bank import metric_slice
     pr = metric_slice(rows=(0, 300), top_k=20)
-    dp, _, _ = device_problem(pr, "f16")
+    dp, op, wq = device_problem(pr, "f16")
     ref = _reference(dp, 20)
-    _check(dp, ref)
+    _check(dp, ref, op, wq)
 
 
 def test_static_power_sum_rejects_oversized_problem():
