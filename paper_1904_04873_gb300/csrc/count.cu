@@ -538,9 +538,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         const int pos_max = 32 * wseg - 33;
         const int pbase = cur.pbase;
 
-        // new region -> new visit buffer
+        // new region -> new visit buffer (the first one opens this CTA's first visit; the
+        // visit before it belongs to another CTA)
         if (!a.dense && cur.region != region) {
-            topk_close_visit<THREADS>(a, visit, ts, sm);
+            if (region >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
             ++visit;
             region = cur.region;
         }
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(THREADS, 1) count_plain(const CountArgs a) {
         const int b = cur.bt * THREADS + tid;
         const bool bvalid = b < P.B;
         if (!a.dense && cur.region != region) {
-            topk_close_visit<THREADS>(a, visit, ts, sm);
+            if (region >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
             ++visit;
             region = cur.region;
         }

@@ -122,9 +122,12 @@ __global__ void __launch_bounds__(WT) weights_kernel(const double* __restrict__ 
         __syncthreads();
         scale = s_scale;
     }
+    // a band of at most TILE SFTs still has its raw weights in shared memory (the FP64 pipe is
+    // narrow on this GPU: forming them once saves half of the kernel's time)
+    const bool staged = norm && N <= TILE;
     double q1 = 0.0, q2 = 0.0;
     for (int i = threadIdx.x; i < N; i += WT) {
-        const double raw = raw_weight(B, arms + 6 * (size_t)i, Sn[i]);
+        const double raw = staged ? s_raw[i] : raw_weight(B, arms + 6 * (size_t)i, Sn[i]);
         const double x = norm ? __dmul_rn(raw, scale) : raw;
         double q;
         const size_t idx = (size_t)s * N + i;

@@ -397,8 +397,10 @@ def main(argv=None):
     a = ap.parse_args(argv)
     import torch
     from . import build
+    from .clocks import ClockSampler
     build.build()
     torch.cuda.set_device(0)
+    sampler = ClockSampler(0).start()
     if a.what == "precision":
         r = precision(n_sky=a.sky or 2000)
     elif a.what == "batching":
@@ -410,6 +412,9 @@ def main(argv=None):
                    m=a.mismatch, ap_block=a.ap_block)
     else:
         r = full(n_sky=a.sky or 100048, n_inj=a.injections, depth_amp=a.amp, n_f0=a.f0)
+    # SM clocks and throttle reasons over the whole experiment (a rate measured under a thermal
+    # or hardware slowdown, or at a clock stuck below its maximum, is not a valid measurement)
+    r["clocks"] = sampler.stop()
     print(json.dumps(r))
 
 

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -542,6 +542,30 @@ def batching(n_patch: int = 64, size_lo: int = 500, size_hi: int = 5000, n_per_d
                                 P_days=np.linspace(15.0, 45.0, n_bin), n_T=n_bin, power_kind=power_kind,
                                 seed=seed + int(f), top_k=1000, patch_start=ps))
     return out
+
+
+def patch_groups(patch_start, n_groups: int) -> List[List[int]]:
+    """The patches of a problem dealt into n_groups groups of about equal sky count:
+    largest patch first, in a snake order over the groups; each group lists its
+    patches in their original order."""
+    ps = np.asarray(patch_start, dtype=np.int64)
+    sizes = np.diff(ps)
+    order = sorted(range(sizes.size), key=lambda p: (-int(sizes[p]), p))
+    groups: List[List[int]] = [[] for _ in range(n_groups)]
+    for k, p in enumerate(order):
+        r, c = divmod(k, n_groups)
+        groups[c if r % 2 == 0 else n_groups - 1 - c].append(p)
+    return [sorted(g) for g in groups if g]
+
+
+def select_patches(pr: Problem, patches: Sequence[int]) -> Problem:
+    """The problem restricted to the listed patches: their sky points in the listed
+    order, one patch each (band, SFTs, powers and binary templates unchanged)."""
+    ps = np.asarray(pr.patch_start, dtype=np.int64)
+    sky = np.concatenate([pr.sky[ps[p]:ps[p + 1]] for p in patches], axis=0)
+    sizes = [int(ps[p + 1] - ps[p]) for p in patches]
+    new_ps = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return dataclasses.replace(pr, sky=np.ascontiguousarray(sky), patch_start=new_ps)
 
 
 def full(n_sky: int = 100048, n_per_det: int = 4000, n_f0: int = 9000, seed: int = SEED_NOISE,

@@ -49,12 +49,7 @@ def test_profile_value_follows_the_kernel_sources(tmp_path):
 def test_committed_summaries_hold_the_figures_bench_reads():
     # (whether their stamp matches the current kernel is bench.py's business: a stale
     # summary gives null figures there, not a failure)
-    for name, key in (("count_batched_mid.md", "traffic_bytes_per_launch"),
-                      ("count_batched_small_full.md", "instr_per_term"),
-                      ("count_batched_small_full.md", "lut_instr_per_term"),
-                      ("count_batched_metric_bank.md", "instr_per_term"),
-                      ("count_batched_metric_bank.md", "traffic_bytes_per_launch"),
-                      ("count_batched_metric_bank.md", "traffic_bytes_per_launch_small")):
+    for name, key in [e for ent in bench.PROFILES.values() for e in ent.values()]:
         text = open(os.path.join(ROOT, "profiles", name)).read()
         vals = dict(l.split(":", 1) for l in text.splitlines() if ":" in l and not l.startswith(("|", " ")))
         assert len(vals.get("kernel_source_sha256_16", "").strip()) == 16, name
@@ -63,19 +58,81 @@ def test_committed_summaries_hold_the_figures_bench_reads():
 
 @pytest.mark.parametrize("kind", ["mid", "small", "eccentric", "metric-small"])
 def test_workload_config(kind):
-    pr = bench.make_problem(kind, 0, obank.template_bank)
-    cfg = bench.workload_config(pr, kind)
+    batches = bench.workload_batches(kind, 0, obank.template_bank)
+    assert len(batches) == 1 and len(batches[0]) == 1
+    pr = batches[0][0]
+    cfg = bench.workload_config(batches, kind)
     assert cfg["workload"].startswith(kind + ":")
-    assert cfg["terms_per_step"] == pr.n_terms == pr.S * pr.B * pr.n_f0 * pr.N
+    assert cfg["terms_per_step"] == cfg["terms_per_cycle"] == pr.n_terms == pr.S * pr.B * pr.n_f0 * pr.N
     if kind.startswith("metric"):
         assert "metric bank" in cfg["workload"] and pr.orbit is not None
-    sub = bench.plain_sample(kind, pr.sky, obank.template_bank)
-    assert sub.S == 4 and sub.B == pr.B and sub.N == pr.N
+    sub = bench.first_points(pr)
+    assert sub.S == 4 and sub.B == pr.B and sub.N == pr.N and list(sub.patch_start) == [0, 4]
+    assert bench.launches_per_step(batches[0]) == 8
+
+
+def test_batching_workload_covers_the_configuration():
+    # the default workload: the 64 uneven patches x 4 bands of the batching construction, dealt
+    # into 8 step groups of about equal sky count that together hold every patch once
+    from paper_1904_04873_gb300 import synth
+    full = synth.batching()
+    batches = bench.workload_batches("batching", 0)
+    assert len(batches) == bench.N_GROUPS and all(len(b) == 4 for b in batches)
+    sizes = np.diff(full[0].patch_start)
+    assert sizes.size == 64 and sizes.min() >= 500 and sizes.max() <= 5000
+    got = []
+    for b in batches:
+        for q, p in enumerate(b):
+            assert p.N == full[q].N and p.n_f0 == full[q].n_f0 and p.B == full[q].B == 512
+            assert np.array_equal(p.patch_start, b[0].patch_start)
+        got.append(b[0].sky)
+    sky = np.concatenate(got)
+    assert sky.shape == full[0].sky.shape
+    # every sky point of the construction exactly once
+    key = lambda a: np.round(a, 12).view([("x", a.dtype), ("y", a.dtype), ("z", a.dtype)]).ravel()
+    assert np.array_equal(np.sort(key(sky)), np.sort(key(full[0].sky)))
+    S = np.array([b[0].S for b in batches])
+    assert S.max() / S.min() < 1.1
+    cfg = bench.workload_config(batches, "batching")
+    assert cfg["terms_per_cycle"] == sum(p.n_terms for p in full)
+    assert cfg["steps_per_cycle"] == 8 and cfg["workload"].startswith("batching:")
+    assert bench.launches_per_step(batches[0]) == 20
+
+
+def test_patch_groups_and_selection():
+    from paper_1904_04873_gb300 import synth
+    ps = np.array([0, 5, 7, 20, 21, 30])
+    groups = synth.patch_groups(ps, 2)
+    assert sorted(p for g in groups for p in g) == [0, 1, 2, 3, 4]
+    pr = synth.mid(n_sky=30, n_per_det=20, n_ap=2, n_P=2, n_T=2, patch_size=30)
+    import dataclasses
+    pr = dataclasses.replace(pr, patch_start=ps)
+    sub = synth.select_patches(pr, [2, 4])
+    assert list(sub.patch_start) == [0, 13, 22]
+    assert np.array_equal(sub.sky, np.concatenate([pr.sky[7:20], pr.sky[21:30]]))
+
+
+def test_launcher_command():
+    cmd = bench.launcher_command(4, ["--steps", "3"], 29555)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=4" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29555" in cmd
+    assert cmd[-3:] == [os.path.join(ROOT, "bench.py"), "--steps", "3"]
+
+
+def test_clock_summary():
+    rows = [["0", "2070", "2070", "400", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["0", "1980", "2070", "900", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+            ["0", "[N/A]", "2070"]]
+    c = bench.summarize_clocks(rows)
+    assert c["sm_mhz"] == 2025.0 and c["sm_max_mhz"] == 2070.0 and c["reasons"] == ["sw_power_cap"]
+    assert c["samples"] == 2
 
 
 def test_ranks_search_rotated_skies():
     pr0 = bench.make_problem("small", 0)
     pr1 = bench.make_problem("small", 1)
+    b1 = bench.workload_batches("batching", 1)
+    assert not np.allclose(b1[0][0].sky, bench.workload_batches("batching", 0)[0][0].sky)
     assert pr0.sky.shape == pr1.sky.shape and not np.allclose(pr0.sky, pr1.sky)
     assert np.allclose(np.linalg.norm(pr1.sky, axis=1), 1.0)
 
@@ -90,3 +147,18 @@ def test_reference_arm_prints_its_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "terms/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_relaunches_itself_for_two_ranks():
+    # --gpus 2 outside torchrun: bench.py starts itself as two ranks (torch.distributed.run);
+    # rank 0 times the oracle and prints the one line, rank 1 exits without work
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "small", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=900,
+                       env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["config"]["parallelism"] == "replicas x2"

@@ -32,7 +32,7 @@ def built():
 
 @pytest.fixture(scope="module")
 def prob():
-    # 2 x 300 SFTs: five 128-SFT stages per item, so every CTA with work has stages 0-4
+    # 2 x 300 SFTs: five 128-SFT stages per item (ten of 64), so every CTA with work has them
     pr = small_mid(n_sky=6, n_per_det=300, n_ap=5, n_P=4, n_T=3, patch_size=3, top_k=40)
     dp, op, wq = device_problem(pr, "f16")
     d, sc = oracle_scores(op, wq)
@@ -44,8 +44,10 @@ def test_expired_wait_reports_timeout_then_recovers(prob, threads, direct):
     pr, dp, d, sc = prob
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=128)
     plan.set_direct(direct)
-    assert plan.tile()["sft_chunk"] == 128
-    for skip in (1, 0, 4):        # a middle stage, the first, the last
+    chunk = plan.tile()["sft_chunk"]          # 128, or 64 where the shared memory asks for it
+    stages = -(-pr.N // chunk)                # stages of a CTA's first item
+    assert stages >= 5
+    for skip in (1, 0, stages - 1):           # a middle stage, the first, the item's last
         plan.set_wait(polls=1 << 14, skip_stage=skip)
         plan.number_count()
         assert bsh.sync_status() == bsh.ERR_TIMEOUT
