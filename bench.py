@@ -62,8 +62,8 @@ def parse(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
     ap.add_argument("--direct", type=int, choices=[-1, 0, 1], default=-1,
                     help="binary term per warp (0) or per term (1); -1 leaves it to the plan / autotuner")
-    ap.add_argument("--acc", type=int, choices=[-1, 0, 1], default=-1,
-                    help="weighted accumulation variant (0 predicated adds, 1 byte table); -1: plan / autotuner")
+    ap.add_argument("--acc", type=int, choices=[-1, 0, 1, 2], default=-1,
+                    help="weighted accumulation (0 predicated adds, 1 byte table, 2 tensor cores); -1: plan / autotuner")
     ap.add_argument("--track", choices=["exact", "lut"], default="exact",
                     help="exact track (default) or the look-up-table approximation of Sec. IV.B")
     return ap.parse_args(argv)
@@ -232,12 +232,12 @@ def code_only(text: str) -> str:
 
 
 def kernel_sha(root: str = ROOT) -> str:
-    """Short hash of the count kernel's sources with comments and whitespace removed, so
+    """Short hash of the count kernels' sources with comments and whitespace removed, so
     that only code changes invalidate a summary (matches the ncu summaries' stamp)."""
     import hashlib
     src = os.path.join(root, "paper_1904_04873_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
+    for f in ("count.cu", "count_tc.cu", "count_common.cuh", "bsh_internal.cuh", "select.cuh"):
         h.update(code_only(open(os.path.join(src, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 

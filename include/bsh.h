@@ -226,16 +226,25 @@ int bsh_autotune(bsh_plan* plan, bsh_stream stream);
 /* Current tile shape: CTA size, SFTs per stage, persistent CTAs in the grid. */
 int bsh_plan_tile(const bsh_plan* plan, int* threads, int* sft_chunk, int* ctas);
 
-/* Weighted-accumulation variant of the batched count (also autotuned):
+/* Weighted-accumulation variant of the batched count:
  * 0 = one predicated FP32 add per term; 1 = per 8 SFTs a table of the 256
  * subset sums of their weights and one lookup per template.  Both sum the
  * same weights in FP32 within 4e-6 relative of their FP64 sum (Kahan
- * compensation across 64-SFT blocks).  bsh_plan_set_accumulate re-derives
- * the SFT stage for the variant's shared-memory layout, re-uploads a bound
- * plan (synchronising the legacy default stream) and drops a recorded graph;
- * not capturable.  A plan that forms its binary terms per term (bsh_plan_direct
- * = 1) keeps variant 0; there the autotuner's second candidate per shape is one
- * CTA per SM with the stage left unshrunk instead. */
+ * compensation across 64-SFT blocks) and are autotuned.  2 = on the tensor
+ * cores: the 0/1 peak matrix of 2048 templates x 32 SFTs times the weights'
+ * fixed-point digits round(2^24 w) in base 16 and a column of ones, in FP8
+ * MMAs accumulated in FP32 without rounding, so the unweighted counts are
+ * exact and the weighted counts are the exact sums of the weights' fixed-point
+ * values rounded once to FP32 (fp16 weights are exact in that fixed point;
+ * others differ from it by at most 2^-25 each, and a weight of 256 or more
+ * records BSH_ERR_RANGE); exact-track BATCHED plans with 256-thread CTAs only
+ * (BSH_ERR_ARG otherwise), one CTA per SM, not autotuned (slower on GB300).
+ * bsh_plan_set_accumulate re-derives the SFT stage for the variant's
+ * shared-memory layout, re-uploads a bound plan (synchronising the legacy
+ * default stream) and drops a recorded graph; not capturable.  A plan that
+ * forms its binary terms per term (bsh_plan_direct = 1) keeps variant 0 in
+ * place of 1; there the autotuner's second candidate per shape is one CTA per
+ * SM with the stage left unshrunk instead. */
 int bsh_plan_set_accumulate(bsh_plan* plan, int variant);
 int bsh_plan_accumulate(const bsh_plan* plan);
 

@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbsh.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["peakgram.cu", "weights.cu", "tables.cu", "count.cu", "toplist.cu", "power.cu", "diagnostics.cu",
-           "plan.cu", "bank.cu", "post.cu"]
+SOURCES = ["peakgram.cu", "weights.cu", "tables.cu", "count.cu", "count_tc.cu", "toplist.cu", "power.cu",
+           "diagnostics.cu", "plan.cu", "bank.cu", "post.cu"]
 
 
 def nvcc() -> str:

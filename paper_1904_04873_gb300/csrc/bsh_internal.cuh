@@ -372,7 +372,7 @@ struct CountArgs {
     int mode;                    // BSH_MODE_*
     int max_n;                   // largest SFT count of the problems
     int wrows;                   // Omega-T rows one warp needs at most
-    int acc_mode;                // weighted accumulation variant of the batched kernel
+    int acc_mode;                // weighted accumulation: 0 predicated adds, 1 byte table, 2 tensor cores
     int lut;                     // 1: look-up-table approximation of the track (BSH_MODE_LUT)
     int direct;                  // 1: C_q formed per term from the staged rows (predicated-add only)
     int wait_polls;              // polls of a staging barrier before a wait gives up (BSH_ERR_TIMEOUT)
@@ -387,6 +387,10 @@ struct TmapSet {
 };
 
 void launch_count(const CountArgs& a, const TmapSet& maps, int grid, int threads, cudaStream_t st);
+// tensor-core accumulation of the batched count (acc_mode 2; count_tc.cu)
+void launch_count_tc(const CountArgs& a, const TmapSet& maps, int grid, cudaStream_t st);
+int count_tc_smem_bytes(int I, int wseg, int ot_max, int wrows, int direct);
+int count_tc_tile();
 int launch_cand_params(const ProbDev* dprob, int first_region, int n_patch, int per_region, const bsh_cand* cands,
                        const int32_t* n_cands, int stat, const bsh_post_params* pp, double* params, double* sig,
                        int32_t* valid, cudaStream_t st);

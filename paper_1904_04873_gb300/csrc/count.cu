@@ -16,84 +16,11 @@
 //
 // The plain form (BSH_MODE_PLAIN) evaluates the FP64 track for every term,
 // sums FP64 weights in FP64, and runs once per sky patch.
-#include <cuda.h>
-
-#include "bsh_internal.cuh"
-#include "select.cuh"
+#include "count_common.cuh"
 
 namespace bsh {
 namespace {
 
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-// Bounded wait on an mbarrier phase: false after `limit` polls (2^22 by default: seconds).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
-    for (int it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (it > 32) __nanosleep(64);
-    }
-    return false;
-}
-
-// Tensor memory (TMEM) holds the per-thread Kahan sums of the weighted counts, which
-// leaves shared memory to the staged chunks.  One warp allocates the CTA's columns and
-// frees them on every exit path; a warp reaches the 32 TMEM lanes of its quarter
-// (warp index mod 4), each thread its own lane, with the 32x32b shape.
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
 // 2 consecutive columns of this thread's lane at taddr and at taddr + 32 (sum, compensation);
 // the wait is in the same statement, so no use of the values can move above it.
 __device__ __forceinline__ void tmem_ld2x2(uint32_t taddr, float* a, float* c) {
@@ -122,34 +49,6 @@ __device__ __forceinline__ void tmem_st2x2(uint32_t taddr, const float* a, const
         : "memory");
 }
 
-// ------------------------------------------------------------ items
-struct Item {
-    int q, s, fb, bt;
-};
-
-// Item order inside a problem: its sky patches in turn; inside a patch, binary tiles,
-// then sky points, then f0 blocks (fastest).  The CTAs sharing a patch's items then walk
-// the binary tiles together, so a tile's orbit-table rows are read from L2 by every sky
-// point of the patch instead of the whole table streaming once per (sky point, f0 block).
-__device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
-    int q = 0;
-    while (q + 1 < a.n_probs && it >= a.probs[q + 1].item_begin) ++q;
-    const ProbDev& P = a.probs[q];
-    const long long loc = it - P.item_begin;
-    const long long per_s = (long long)P.n_fb * P.n_bt;
-    const int patch = P.patch_of_s[loc / per_s];         // a patch spans [start, end) x per_s items
-    const long long p0 = P.patch_start[patch];
-    const long long per_bt = (P.patch_start[patch + 1] - p0) * P.n_fb;
-    const long long off = loc - p0 * per_s;
-    Item r;
-    r.q = q;
-    r.bt = (int)(off / per_bt);
-    const int rem = (int)(off - (long long)r.bt * per_bt);
-    r.s = (int)p0 + rem / P.n_fb;
-    r.fb = rem % P.n_fb;
-    return r;
-}
-
 // Shared-memory layout of the batched kernel: double-buffered TMA stages
 // (peakgram band, vn / weight / c table rows), per-warp track values, the
 // TMEM address slot, stage barriers and arrival counters, and the
@@ -157,16 +56,6 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
 struct Layout {
     int pk[2], vn[2], w[2], c[2], y, cp, ce, sl, tab, bar, done, tm, sel, misc, total;
 };
-
-__host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
-
-constexpr int SCAP = 8;   // deferred near-boundary entries per thread and SFT chunk
-
-// Row stride (32-bit words) of the staged c_q rows: the chunk plus four words, so that
-// threads of a warp reading one SFT of up to 8 consecutive orbit rows hit distinct
-// shared-memory banks (the TMA box of the table is this wide; a 256-SFT chunk, at the
-// box limit, is not padded).
-__host__ __device__ __forceinline__ int c_stride(int I) { return I < 256 ? I + 4 : I; }
 
 // direct: the C values are formed per term from the staged c_q rows (no per-warp arrays).
 __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int wrows, int threads, int acc,
@@ -192,80 +81,6 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     return L;
 }
 
-struct TopSmem {
-    unsigned long long tau;
-    int count;
-    int have_tau;
-    float mean, inv_sig;
-    int abort;
-};
-
-// Per-item constants shared by every thread.
-struct ItemCtx {
-    int q, s, fb, bt, j0, jb, c0, pbase, ot0, nrows, F2a, F2r, region, nchunks;
-    uint32_t lid_base;
-};
-
-__device__ __forceinline__ ItemCtx item_ctx(const CountArgs& a, const Item& it, int THREADS) {
-    const ProbDev& P = a.probs[it.q];
-    ItemCtx c;
-    c.q = it.q;
-    c.s = it.s;
-    c.fb = it.fb;
-    c.bt = it.bt;
-    c.j0 = it.fb * P.JB;
-    c.jb = imin(P.JB, P.n_f0 - c.j0);
-    const int Gj0 = P.G0 + c.j0;
-    int lo_bin = Gj0 + P.o_min - 1 - P.k_lo;
-    lo_bin = lo_bin < 0 ? 0 : lo_bin;
-    c.c0 = (lo_bin >> 5) & ~3;
-    c.pbase = Gj0 - P.k_lo - 32 * c.c0;
-    const int b0 = it.bt * THREADS;
-    const int b1 = imin(b0 + THREADS, P.B) - 1;
-    c.ot0 = P.brow[b0];
-    c.nrows = P.brow[b1] - c.ot0 + 1;
-    c.F2a = (int)llrint(2.0 * P.F0) + 2 * c.j0;
-    c.F2r = c.F2a + 2 * ((c.jb - 1) / 2);   // 2 F of the block's middle template (LUT reference)
-    const int patch = P.patch_of_s[it.s];
-    c.region = P.region_base + patch;
-    c.lid_base = (uint32_t)((long long)(it.s - (int)P.patch_start[patch]) * P.B);
-    c.nchunks = (P.N + a.chunk - 1) / a.chunk;
-    return c;
-}
-
-// Sequence number of the stage whose copies are in flight into buffer b, or -1: entries
-// 2 and 3 of the `done` words.
-__device__ __forceinline__ int* inflight_slots(unsigned char* smem, const Layout& L) {
-    return reinterpret_cast<int*>(smem + L.done) + 2;
-}
-
-// Issues the TMA / bulk copies of chunk `ch` of item `c` into buffer `buf`; `seq` is the
-// stage's sequence number within the CTA.  The stage numbered a.skip_stage (a test hook,
-// normally -1) is left unissued: nothing completes its barrier phase, so the wait on it
-// expires.
-__device__ __forceinline__ void issue_stage(const CountArgs& a, const TmapSet& maps, const ItemCtx& c, int ch,
-                                            unsigned char* smem, const Layout& L, int buf, int seq) {
-    int* inflight = inflight_slots(smem, L);
-    if (seq == a.skip_stage) {
-        inflight[buf] = -1;
-        return;
-    }
-    inflight[buf] = seq;
-    const ProbDev& P = a.probs[c.q];
-    const int I = a.chunk;
-    const int i0 = ch * I;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar) + buf;
-    // the c_q box holds P.crows rows from the item's first row (rows past the table
-    // are zero-filled and still count toward the expected bytes)
-    const uint32_t bytes = (uint32_t)(I * a.wseg_max * 4 + I * 4 * 2 + c_stride(I) * P.crows * 4);
-    fence_proxy_async();
-    mbar_arrive_expect_tx(bar, bytes);
-    tma_load_2d(smem + L.pk[buf], maps.map[c.q], bar, c.c0, i0);
-    tma_load_2d(smem + L.c[buf], maps.cmap[c.q], bar, i0, c.ot0);
-    bulk_load(smem + L.vn[buf], P.vn_q + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
-    bulk_load(smem + L.w[buf], P.w32 + (size_t)c.s * P.Np + i0, (uint32_t)(I * 4), bar);
-}
-
 // 8 x 8 bit-matrix transpose: byte u of x is row u (bit k = column k); on
 // return byte k holds column k (bit u = bit k of the input's byte u).
 __device__ __forceinline__ uint64_t transpose8x8(uint64_t x) {
@@ -283,34 +98,6 @@ __device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32
     const uint32_t u = a ^ b;
     h = (a & b) | (u & c);
     l = u ^ c;
-}
-
-// Template-by-template decision of one block at one SFT (rare): the ends are near a
-// rounding boundary; FP64 decides the templates within 31 M of it.
-__device__ __forceinline__ uint32_t slow_window_exact(const ProbDev& P, int v0, int v1, int pbase, int pos_max,
-                                                   const uint32_t* row, int s, int b, int i, int j0,
-                                                   unsigned* status) {
-    bool have = false;
-    double D = 0.0;
-    auto exact_o = [&](int j) -> int {
-        if (!have) {
-            const double* n = P.sky + 3 * (size_t)s;
-            const double* v = P.v + 3 * (size_t)i;
-            const double vn = __dadd_rn(__dadd_rn(__dmul_rn(v[0], n[0]), __dmul_rn(v[1], n[1])),
-                                        __dmul_rn(v[2], n[2]));
-            const double c = P.c64[(size_t)P.brow[b] * P.Np + i];
-            D = __dsub_rn(vn, __dmul_rn(P.bap[b], c));
-            have = true;
-        }
-        const double F = P.F0 + (double)(j0 + j);
-        const double x = __dadd_rn(F, __dmul_rn(F, D));
-        const double k = floor(__dadd_rn(x, 0.5));
-        return (int)((long long)k - (long long)(P.G0 + j0 + j));
-    };
-    bool bad = false;
-    const uint32_t m = fp_window_exact(v0, v1, pbase, pos_max, P.fp.s_y, P.fp.M, row, exact_o, &bad);
-    if (bad) set_status(status, ST_RANGE);
-    return m;
 }
 
 // Exact FP64 fallback of the look-up-table variant: the modulation at the block's
@@ -331,40 +118,6 @@ __device__ __noinline__ uint32_t slow_window_lut(const ProbDev& P, int pbase, in
         return 0u;
     }
     return row_window(row, pos);
-}
-
-// ------------------------------------------------------------ toplist pieces
-template <int THREADS>
-__device__ void topk_reduce(const CountArgs& a, Entry* buf, int keep, TopSmem& ts, SelectSmem& sm) {
-    const int n = ts.count;
-    __syncthreads();
-    if (n <= keep) return;
-    auto seg = [&](int, const Entry*& base, int& cnt) {
-        base = buf;
-        cnt = n;
-    };
-    const unsigned long long tau = cta_kth_largest<THREADS>(1, seg, keep, sm);
-    const int m = cta_compact_ge<THREADS>(buf, n, tau, sm);
-    if (threadIdx.x == 0) {
-        ts.count = m;
-        ts.tau = tau;
-        ts.have_tau = 1;
-    }
-    __syncthreads();
-}
-
-template <int THREADS>
-__device__ void topk_close_visit(const CountArgs& a, int visit, TopSmem& ts, SelectSmem& sm) {
-    if (visit < 0) return;
-    Entry* buf = a.visit_buf + (size_t)visit * a.cap;
-    topk_reduce<THREADS>(a, buf, a.top_k, ts, sm);
-    if (threadIdx.x == 0) {
-        a.visit_count[visit] = ts.count;
-        ts.count = 0;
-        ts.have_tau = 0;
-        ts.tau = 0ull;
-    }
-    __syncthreads();
 }
 
 // Scores the 32 templates of this thread and appends the ones above the
@@ -438,22 +191,6 @@ __device__ __forceinline__ void kahan_fold(float* part, uint32_t tacc) {
         }
         tmem_st2x2(tacc + (uint32_t)j0, a, c);
     }
-}
-
-// Chunk `ch + ahead` of the item sequence starting at `it`: returns false past the CTA's range.
-__device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, int ch, int ahead, long long it_end,
-                                              int threads, ItemCtx* out, int* out_ch) {
-    ItemCtx c = item_ctx(a, decode_item(a, it), threads);
-    int k = ch + ahead;
-    while (k >= c.nchunks) {
-        k -= c.nchunks;
-        ++it;
-        if (it >= it_end) return false;
-        c = item_ctx(a, decode_item(a, it), threads);
-    }
-    *out = c;
-    *out_ch = k;
-    return true;
 }
 
 // ACC selects the weighted accumulation: 0 = one predicated FP32 add per term;

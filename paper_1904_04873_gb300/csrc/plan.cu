@@ -169,7 +169,7 @@ struct bsh_plan {
     int regions = 0, visits = 0, visit_cap = 0;
     size_t ws_cap = 0;                     // workspace bytes: the largest of the tuning candidates
     double tuned_rate = 0.0;
-    int acc_mode = 0;                      // weighted accumulation variant (autotuned)
+    int acc_mode = 0;                      // weighted accumulation variant (autotuned); 2 = tensor cores
     int direct_opt = -1;                   // per-term C values: -1 automatic, 0 off, 1 on
     int direct = 0;                        // the choice in effect
     int direct_tuned = -1;                 // the autotuner's choice under direct_opt = -1 (-1: none yet)
@@ -198,6 +198,12 @@ struct bsh_plan {
 namespace {
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Binary templates per work item: the CTA size, or the tensor-core kernel's fixed tile.
+int tile_b(const bsh_plan* p) { return p->acc_mode == 2 ? count_tc_tile() : p->threads; }
+
+// Whether the tensor-core accumulation applies: the exact-track batched count with 256-thread CTAs.
+bool tc_ok(const bsh_plan* p) { return p->mode == BSH_MODE_BATCHED && !p->lut && p->threads == 256; }
 
 // Tile shapes the autotuner considers (the first is the default).
 std::vector<int> tune_threads(const bsh_plan* p) {
@@ -295,7 +301,7 @@ int prepare_problem(bsh_plan* p, ProbHost& h) {
     const int nb = (d.n_f0 + JW - 1) / JW;
     pd.JB = (d.n_f0 + nb - 1) / nb;
     pd.n_fb = (d.n_f0 + pd.JB - 1) / pd.JB;
-    pd.n_bt = (pd.B + p->threads - 1) / p->threads;
+    pd.n_bt = (pd.B + tile_b(p) - 1) / tile_b(p);
     pd.p_th = std::exp(-d.rho_th);
     pd.v_max = d.v_max;
     // patch template counts must fit a 32-bit local id
@@ -446,12 +452,12 @@ int bsh_plan_create(const bsh_problem* problems, int n_problems, const bsh_count
     int first_rc = -1;
     for (int t : tune_threads(p))
         for (int c : tune_chunks(p))
-            for (int v = 0; v < 8; ++v) {
+            for (int v = 0; v < 12; ++v) {
                 p->threads = t;
                 p->chunk = c;
-                p->acc_mode = v & 1;
-                p->one_cta = (v >> 1) & 1;
-                p->direct_tuned = v >> 2;
+                p->acc_mode = v % 3;
+                p->one_cta = (v / 3) & 1;
+                p->direct_tuned = v / 6;
                 const int rc = build_schedule(p);
                 if (first_rc < 0) first_rc = rc;
                 if (rc == BSH_OK) cap = std::max(cap, p->ws_size);
@@ -491,14 +497,15 @@ int bsh_plan_first_region(const bsh_plan* p, int q) {
 namespace {
 
 int build_schedule(bsh_plan* p, long long item_limit) {
+    if (p->acc_mode == 2 && !tc_ok(p)) p->acc_mode = 0;
     // tile shapes
     p->ot_max = 1;
     p->wrows = 1;
     // orbit rows spanned by one binary tile (CTA) and by one warp's 32 templates
     for (auto& h : p->P) {
         const int B = (int)h.brow.size();
-        for (int b0 = 0; b0 < B; b0 += p->threads) {
-            const int b1 = std::min(b0 + p->threads, B) - 1;
+        for (int b0 = 0; b0 < B; b0 += tile_b(p)) {
+            const int b1 = std::min(b0 + tile_b(p), B) - 1;
             p->ot_max = std::max(p->ot_max, h.brow[b1] - h.brow[b0] + 1);
             for (int w0 = b0; w0 <= b1; w0 += 32) {
                 const int w1 = std::min(w0 + 31, B - 1);
@@ -509,7 +516,8 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     // orbit rows shared by few templates (banks): form C per term rather than per warp
     const bool auto_direct = p->direct_tuned >= 0 ? p->direct_tuned == 1 : p->wrows > 4;
     p->direct = p->mode == BSH_MODE_BATCHED && (p->direct_opt == 1 || (p->direct_opt < 0 && auto_direct)) ? 1 : 0;
-    if (p->direct) p->acc_mode = 0;   // the per-term variant accumulates by predicated adds only
+    // the per-term variant accumulates by predicated adds or on the tensor cores
+    if (p->direct && p->acc_mode == 1) p->acc_mode = 0;
     int region = 0;
     long long items = 0;
     for (auto& h : p->P) {
@@ -529,8 +537,9 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     const bool one = p->one_cta || p->opt.ctas_per_sm == 1;
     bool fits_two = false;
     while (!one) {
-        p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
-                                   p->direct);
+        p->smem = p->acc_mode == 2 ? count_tc_smem_bytes(p->chunk, p->wseg_max, p->ot_max, p->wrows, p->direct)
+                                   : count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads,
+                                                      p->acc_mode, p->direct);
         fits_two = p->smem <= smem_two;
         if (fits_two || p->chunk <= 32) break;
         p->chunk /= 2;
@@ -538,8 +547,9 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     if (!fits_two) {
         p->chunk = chunk0;
         while (true) {
-            p->smem = count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows, p->threads, p->acc_mode,
-                                   p->direct);
+            p->smem = p->acc_mode == 2 ? count_tc_smem_bytes(p->chunk, p->wseg_max, p->ot_max, p->wrows, p->direct)
+                                       : count_smem_bytes(p->mode, p->chunk, p->wseg_max, p->ot_max, p->wrows,
+                                                          p->threads, p->acc_mode, p->direct);
             if (p->smem <= smem_one || p->chunk <= 32) break;
             p->chunk /= 2;
         }
@@ -642,7 +652,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         for (int v : rvis[r]) p->region_visits.push_back(v);
     }
     p->region_visit_off[p->regions] = (int)p->region_visits.size();
-    p->cap = 2 * k + p->threads * JW;
+    p->cap = 2 * k + tile_b(p) * JW;
     // workspace layout
     size_t o = 0;
     p->off_probs = o; o = al(o + sizeof(ProbDev) * p->n);
@@ -755,7 +765,8 @@ int run_count(bsh_plan* p, int dense, cudaStream_t st) {
     for (int q = 0; q < p->n; ++q) launch_tables(p->P[q].pd, dprobs + q, p->mode, sp, st);
     CountArgs a = count_args(p, dense);
     if (p->mode == BSH_MODE_BATCHED) {
-        launch_count(a, p->maps, p->ctas, p->threads, st);
+        if (p->acc_mode == 2) launch_count_tc(a, p->maps, p->ctas, st);
+        else launch_count(a, p->maps, p->ctas, p->threads, st);
     } else {
         for (int r = 0; r < p->regions; ++r) {
             if (p->pl_ctas[r] == 0) continue;
@@ -895,7 +906,8 @@ int bsh_autotune(bsh_plan* p, bsh_stream stream) {
                 const ProbDev& pd = p->P[q].pd;
                 int fb, bt;
                 item_fb_bt(p->P[q], it - pd.item_begin, &fb, &bt);
-                const int nb = std::min(t, pd.B - bt * t);
+                const int tb = tile_b(p);
+                const int nb = std::min(tb, pd.B - bt * tb);
                 const int jb = std::min(pd.JB, pd.n_f0 - fb * pd.JB);
                 terms += (double)nb * jb * pd.N;
             }
@@ -955,7 +967,8 @@ int bsh_plan_tile(const bsh_plan* p, int* threads, int* sft_chunk, int* ctas) {
 }
 
 int bsh_plan_set_accumulate(bsh_plan* p, int variant) {
-    if (!p || (variant != 0 && variant != 1)) return BSH_ERR_ARG;
+    if (!p || variant < 0 || variant > 2) return BSH_ERR_ARG;
+    if (variant == 2 && !tc_ok(p)) return BSH_ERR_ARG;
     p->acc_mode = variant;
     p->one_cta = 0;
     p->chunk = tune_chunks(p)[0];

@@ -101,6 +101,20 @@ def test_wait_limit_arguments(small):
     L.bsh_plan_destroy(h)
 
 
+def test_tensor_accumulation_needs_the_exact_batched_256_thread_plan(small):
+    L = bsh.lib()
+    fp = FakeProblem(small)
+    rc, h = create([fp.d])
+    assert rc == bsh.OK and L.bsh_plan_set_accumulate(h, 2) == bsh.OK and L.bsh_plan_accumulate(h) == 2
+    assert L.bsh_plan_set_accumulate(h, 3) == bsh.ERR_ARG
+    L.bsh_plan_destroy(h)
+    for opt in (dict(threads=128), dict(mode=bsh.MODE_LUT), dict(mode=bsh.MODE_PLAIN)):
+        rc, h = create([fp.d], **opt)
+        assert rc == bsh.OK
+        assert L.bsh_plan_set_accumulate(h, 2) == bsh.ERR_ARG
+        L.bsh_plan_destroy(h)
+
+
 def test_plain_plan(small):
     fp = FakeProblem(small)
     rc, h = create([fp.d], mode=bsh.MODE_PLAIN)

@@ -24,7 +24,7 @@ def test_code_only_ignores_comments_and_layout():
 def _fake_tree(tmp_path, body="int k;"):
     src = tmp_path / "paper_1904_04873_gb300" / "csrc"
     src.mkdir(parents=True)
-    for f in ("count.cu", "bsh_internal.cuh", "select.cuh"):
+    for f in ("count.cu", "count_tc.cu", "count_common.cuh", "bsh_internal.cuh", "select.cuh"):
         (src / f).write_text(f"// {f}\n{body}\n")
     (tmp_path / "profiles").mkdir()
     return src

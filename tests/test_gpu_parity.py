@@ -104,10 +104,11 @@ def test_count_dense_batched(mid_small, dtype):
 
 
 @pytest.mark.parametrize("threads,chunk,acc,direct", [(128, 64, 0, 1), (256, 256, 0, 1), (256, 64, 0, 0),
-                                                      (128, 256, 1, 0), (256, 64, 1, 0), (256, 128, 1, 0)])
+                                                      (128, 256, 1, 0), (256, 64, 1, 0), (256, 128, 1, 0),
+                                                      (256, 128, 2, 0), (256, 64, 2, 1), (256, 256, 2, 0)])
 def test_count_dense_tile_shapes(mid_small, threads, chunk, acc, direct):
     # every accumulation variant and both ways of forming the binary term (the byte-table
-    # accumulation exists only with the per-warp term)
+    # accumulation exists only with the per-warp term; the tensor-core one with 256 threads)
     pr = mid_small
     dp, op, wq = device_problem(pr, "f16")
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=chunk)

@@ -39,11 +39,14 @@ def prob():
     return pr, dp, d, sc
 
 
-@pytest.mark.parametrize("threads,direct", [(256, 0), (128, 0), (256, 1)])
-def test_expired_wait_reports_timeout_then_recovers(prob, threads, direct):
+@pytest.mark.parametrize("threads,direct,acc", [(256, 0, 0), (128, 0, 0), (256, 1, 0), (256, 0, 2), (256, 1, 2)])
+def test_expired_wait_reports_timeout_then_recovers(prob, threads, direct, acc):
+    # acc 2: the tensor-core kernel, whose exit path also waits for its MMAs in flight
     pr, dp, d, sc = prob
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=threads, sft_chunk=128)
     plan.set_direct(direct)
+    plan.set_accumulate(acc)
+    assert plan.tile()["accumulate"] == acc
     chunk = plan.tile()["sft_chunk"]          # 128, or 64 where the shared memory asks for it
     stages = -(-pr.N // chunk)                # stages of a CTA's first item
     assert stages >= 5
