@@ -60,6 +60,7 @@ def parse(argv=None):
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM of the persistent grid (0: the plan's choice)")
     ap.add_argument("--direct", type=int, choices=[-1, 0, 1], default=-1,
                     help="binary term per warp (0) or per term (1); -1 leaves it to the plan / autotuner")
     ap.add_argument("--acc", type=int, choices=[-1, 0, 1, 2], default=-1,
@@ -260,7 +261,7 @@ def profile_value(name: str, key: str, root: str = ROOT):
 # per term ("ipt") and its DRAM bytes per launch ("traffic"): (file, key)
 PROFILES = {"batching": {"ipt": ("count_batched_batching.md", "instr_per_term"),
                          "traffic": ("count_batched_batching.md", "traffic_bytes_per_launch")},
-            "mid": {"ipt": ("count_batched_small_full.md", "instr_per_term"),
+            "mid": {"ipt": ("count_batched_mid.md", "instr_per_term"),
                     "traffic": ("count_batched_mid.md", "traffic_bytes_per_launch")},
             "metric": {"ipt": ("count_batched_metric_bank.md", "instr_per_term"),
                        "traffic": ("count_batched_metric_bank.md", "traffic_bytes_per_launch")},
@@ -423,7 +424,8 @@ def main(argv=None):
     for dpb in dps:
         for dp in dpb:
             dp.prepare()
-        plan = bsh.Plan(dpb, mode, top_k=dpb[0].pr.top_k, threads=args.threads, sft_chunk=args.chunk)
+        plan = bsh.Plan(dpb, mode, top_k=dpb[0].pr.top_k, threads=args.threads, sft_chunk=args.chunk,
+                        ctas_per_sm=args.ctas)
         if args.direct >= 0:
             plan.set_direct(args.direct)
         if args.acc >= 0:

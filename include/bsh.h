@@ -185,7 +185,8 @@ typedef struct bsh_count_options {
     int top_k;                 /* toplist length per patch (N_C of Sec. IV.C), 1..16384 */
     int threads;               /* CTA size: 0 = autotuned / default, else 128 or 256 */
     int sft_chunk;             /* SFTs per shared-memory stage: 0 = default, else 64, 128 or 256 */
-    int ctas_per_sm;           /* 0 = default */
+    int ctas_per_sm;           /* 0 = default; > 1 also sizes the SFT stage so that this many CTAs
+                                  fit an SM's shared memory */
 } bsh_count_options;
 
 typedef struct bsh_plan bsh_plan;

@@ -531,7 +531,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     // chunk size: shrink until the CTAs that the register budget allows per SM
     // (512 threads) also fit its shared memory; else (or when one CTA per SM is
     // asked for) settle for one CTA per SM
-    const int blocks_target = 512 / p->threads;
+    const int blocks_target = p->opt.ctas_per_sm > 1 ? p->opt.ctas_per_sm : 512 / p->threads;
     const int smem_two = (227 * 1024) / blocks_target - 1024, smem_one = 220 * 1024;
     const int chunk0 = p->chunk;
     const bool one = p->one_cta || p->opt.ctas_per_sm == 1;
