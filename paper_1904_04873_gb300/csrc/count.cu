@@ -221,11 +221,23 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     uint8_t* slist = reinterpret_cast<uint8_t*>(smem + L.sl);                     // [SCAP][THREADS]
     float* tab = reinterpret_cast<float*>(smem + L.tab) + warp * 256;
 
-    long long it = a.cta_item[blockIdx.x];
-    const long long it_end = a.cta_item[blockIdx.x + 1];
-    if (it >= it_end) return;
-    int visit = a.cta_visit[blockIdx.x] - 1;
-    int region = -1;
+    int member;
+    const int pq = cta_pool(a, &member);
+    const Walk wk = pool_walk(a, pq);
+    if (tid == 0) {   // the CTA's first item
+        ts.q_tail = 0;
+        ts.q_done = 0;
+        long long s0;
+        (void)pool_take(a, pq, wk, ts, 0, &s0);
+    }
+    __syncthreads();
+    if (ts.q_tail == 0) return;   // the other CTA of the pool took every item
+    int head = 0;                 // this CTA's item number
+    long long step = ts.q_step[0];  // walk step of the current item
+    int visit = -1;
+    int run = a.pool_run[pq];     // run (one region along the pool's walk) of the current item
+    const int run_end = a.pool_run[pq + 1];
+    int open_run = -1;
 
     // TMEM for the Kahan sums: 64 columns per warp quarter-slot (256 threads: warps w and
     // w + 4 share lanes, so 128 columns; 128 threads: 64)
@@ -249,12 +261,12 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
     __syncthreads();
     tmem_fence_after();
 
-    ItemCtx cur = item_ctx(a, decode_item(a, it), THREADS);
+    ItemCtx cur = item_ctx(a, decode_item(a, walk_item(wk, step)), THREADS);
     if (tid == 0) {
         issue_stage(a, maps, cur, 0, smem, L, 0, 0);
         ItemCtx nx;
         int nch;
-        if (advance_chunk(a, it, 0, 1, it_end, THREADS, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1, 1);
+        if (advance_chunk(a, pq, wk, ts, 0, 0, 1, THREADS, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1, 1);
     }
     unsigned g = 0;   // chunk sequence number within this CTA
 
@@ -275,12 +287,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         const int pos_max = 32 * wseg - 33;
         const int pbase = cur.pbase;
 
-        // new region -> new visit buffer (the first one opens this CTA's first visit; the
-        // visit before it belongs to another CTA)
-        if (!a.dense && cur.region != region) {
-            if (region >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
-            ++visit;
-            region = cur.region;
+        // new run of the pool's walk -> new visit buffer (the run's buffer of this member)
+        if (!a.dense) {
+            while (run + 1 < run_end && step >= a.run_step[run + 1]) ++run;
+            if (run != open_run) {
+                if (open_run >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
+                visit = 2 * run + member;
+                open_run = run;
+            }
         }
         if (tid == 0) {
             const double sw = P.sum_w[cur.s], sw2 = P.sum_w2[cur.s];
@@ -499,9 +513,10 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
                 __threadfence_block();   // this warp's reads of the buffer precede its arrival
                 const unsigned prev = atomicAdd(&done[buf], 1u);
                 if (prev == NW * ((g >> 1) + 1) - 1) {
+                    __threadfence_block();   // the previous issuer's writes of the item ring
                     ItemCtx nx;
                     int nch;
-                    if (advance_chunk(a, it, ch, 2, it_end, THREADS, &nx, &nch))
+                    if (advance_chunk(a, pq, wk, ts, head, ch, 2, THREADS, &nx, &nch))
                         issue_stage(a, maps, nx, nch, smem, L, buf, (int)g + 2);
                 }
             }
@@ -529,12 +544,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
         if (__syncthreads_or(ts.abort)) break;   // a wait expired somewhere: leave together
         emit_item<THREADS>(a, P, cur, b, bvalid, nw, nu, visit, ts, sm);
 
-        ++it;
-        if (it >= it_end) break;
-        cur = item_ctx(a, decode_item(a, it), THREADS);
+        // the last chunk's issuer has taken the next item or found the pool exhausted
+        ++head;
+        if (head >= ts.q_tail) break;
+        step = ts.q_step[head & 3];
+        cur = item_ctx(a, decode_item(a, walk_item(wk, step)), THREADS);
         __syncthreads();
     }
-    if (!ts.abort && !a.dense) topk_close_visit<THREADS>(a, visit, ts, sm);
+    if (!ts.abort && !a.dense && open_run >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
     // after an expired wait, copies issued into the other buffer may still be landing in this
     // CTA's shared memory: wait (bounded) for every stage still marked in flight before the
     // CTA exits (every warp is past its last issue: they all met at the exit barrier)

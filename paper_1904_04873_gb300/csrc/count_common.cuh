@@ -87,27 +87,74 @@ struct Item {
     int q, s, fb, bt;
 };
 
-// Item order inside a problem: its sky patches in turn; inside a patch, binary tiles,
-// then sky points, then f0 blocks (fastest).  The CTAs sharing a patch's items then walk
-// the binary tiles together, so a tile's orbit-table rows are read from L2 by every sky
-// point of the patch instead of the whole table streaming once per (sky point, f0 block).
+// Item order inside a problem: sky points in turn (so a sky patch, a contiguous run of sky
+// points, is a contiguous run of items); inside a sky point, binary tiles, then f0 blocks
+// (fastest).
 __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
     int q = 0;
     while (q + 1 < a.n_probs && it >= a.probs[q + 1].item_begin) ++q;
     const ProbDev& P = a.probs[q];
     const long long loc = it - P.item_begin;
     const long long per_s = (long long)P.n_fb * P.n_bt;
-    const int patch = P.patch_of_s[loc / per_s];         // a patch spans [start, end) x per_s items
-    const long long p0 = P.patch_start[patch];
-    const long long per_bt = (P.patch_start[patch + 1] - p0) * P.n_fb;
-    const long long off = loc - p0 * per_s;
     Item r;
     r.q = q;
-    r.bt = (int)(off / per_bt);
-    const int rem = (int)(off - (long long)r.bt * per_bt);
-    r.s = (int)p0 + rem / P.n_fb;
-    r.fb = rem % P.n_fb;
+    r.s = (int)(loc / per_s);
+    const int rem = (int)(loc - (long long)r.s * per_s);
+    r.bt = rem / P.n_fb;
+    r.fb = rem - r.bt * P.n_fb;
     return r;
+}
+
+// Work of the batched kernels.  CTAs c and c + pools (c < pools) share pool c: a contiguous,
+// cost-balanced range [base, base + len) of the item list, walked in a fixed order (below),
+// from which the two CTAs take one item at a time with an atomic counter.  Of the two CTAs
+// resident on an SM, the warp schedulers favour one; with fixed ranges the favoured one
+// finishes early and the other runs on alone at a fraction of the SM's issue rate.  A pool
+// pairs an early CTA with a late one, and the pair ends together.
+//
+// The walk covers the range in sweeps of P items (one sky point's binary tiles and f0
+// blocks).  Sweep j covers the items [base + jP, base + (j+1)P), started at offset r (the
+// first tile of the next sky point) and wrapped round, so every pool of a problem meets
+// binary tile t at about the same time and the tile's orbit rows are read from DRAM about
+// once per sweep instead of once per sky point.  A last, partial sweep of m < P items that
+// does not reach the next sky point (m <= r) holds tiles [P - r, P - r + m) of one sky point:
+// it starts at the tile that is a multiple of m, so that at step x of that sweep every such
+// pool is on the tile of residue x mod m (one of two tiles), and the pools whose last sweep
+// wraps are on tile x or x + P - m.  r = 0 walks the range in order.
+struct Walk {
+    long long base, len;
+    long long P;
+    long long r;
+};
+
+// Pool of this CTA and its member index (0 or 1) in the pool.
+__device__ __forceinline__ int cta_pool(const CountArgs& a, int* member) {
+    const int c = (int)blockIdx.x;
+    *member = c >= a.pools ? 1 : 0;
+    return c >= a.pools ? c - a.pools : c;
+}
+
+__device__ __forceinline__ Walk pool_walk(const CountArgs& a, int q) {
+    Walk w;
+    w.base = a.pool_item[q];
+    w.len = a.pool_item[q + 1] - w.base;
+    w.r = a.pool_sweep[2 * q];
+    w.P = a.pool_sweep[2 * q + 1];
+    return w;
+}
+
+// Item of step k (0 <= k < len) of the walk.
+__device__ __forceinline__ long long walk_item(const Walk& w, long long k) {
+    if (w.r == 0) return w.base + k;
+    const long long j = k / w.P, i = k - j * w.P;
+    const long long m = w.len - j * w.P < w.P ? w.len - j * w.P : w.P;   // items in this sweep
+    const long long e = m > w.r ? m - w.r : 0;                         // of them at offsets >= r
+    if (e == 0 && m < w.P) {                                           // partial, inside one sky point
+        const long long rho = (m - (w.P - w.r) % m) % m;
+        const long long o = i + rho < m ? i + rho : i + rho - m;
+        return w.base + j * w.P + o;
+    }
+    return w.base + j * w.P + (i < e ? w.r + i : i - e);
 }
 
 __host__ __device__ __forceinline__ int align128(int x) { return (x + 127) & ~127; }
@@ -126,6 +173,11 @@ struct TopSmem {
     int have_tau;
     float mean, inv_sig;
     int abort;
+    // batched kernels: the walk steps this CTA has taken from its pool, a ring indexed by the
+    // CTA's item number (written by the one thread issuing a stage, read by all after a barrier)
+    long long q_step[4];
+    int q_tail;                  // items taken so far
+    int q_done;                  // the pool has no items left
 };
 
 // Per-item constants shared by every thread.
@@ -259,19 +311,39 @@ __device__ void topk_close_visit(const CountArgs& a, int visit, TopSmem& ts, Sel
     __syncthreads();
 }
 
-// Chunk `ch + ahead` of the item sequence starting at `it`: returns false past the CTA's range.
-__device__ __forceinline__ bool advance_chunk(const CountArgs& a, long long it, int ch, int ahead, long long it_end,
-                                              int threads, ItemCtx* out, int* out_ch) {
-    ItemCtx c = item_ctx(a, decode_item(a, it), threads);
-    int k = ch + ahead;
-    while (k >= c.nchunks) {
-        k -= c.nchunks;
-        ++it;
-        if (it >= it_end) return false;
-        c = item_ctx(a, decode_item(a, it), threads);
+// Walk step of the CTA's item number x (x <= items taken so far): takes the next item of the
+// pool when x is one past the last taken.  Returns false once the pool is exhausted.
+__device__ __forceinline__ bool pool_take(const CountArgs& a, int q, const Walk& w, TopSmem& ts, int x,
+                                          long long* step) {
+    if (x >= ts.q_tail) {
+        if (ts.q_done) return false;
+        const long long s = (long long)atomicAdd(a.pool_next + q, 1ull);
+        if (s >= w.len) {
+            ts.q_done = 1;
+            return false;
+        }
+        ts.q_step[x & 3] = s;
+        ts.q_tail = x + 1;
+    }
+    *step = ts.q_step[x & 3];
+    return true;
+}
+
+// Chunk `ch + ahead` of the CTA's item sequence from its item number x, taking items from the
+// pool as needed (at most two past x): returns false past the pool's end.
+__device__ __forceinline__ bool advance_chunk(const CountArgs& a, int q, const Walk& w, TopSmem& ts, int x, int ch,
+                                              int ahead, int threads, ItemCtx* out, int* out_ch) {
+    ItemCtx c = item_ctx(a, decode_item(a, walk_item(w, ts.q_step[x & 3])), threads);
+    int n = ch + ahead;
+    while (n >= c.nchunks) {
+        n -= c.nchunks;
+        ++x;
+        long long st;
+        if (!pool_take(a, q, w, ts, x, &st)) return false;
+        c = item_ctx(a, decode_item(a, walk_item(w, st)), threads);
     }
     *out = c;
-    *out_ch = k;
+    *out_ch = n;
     return true;
 }
 

@@ -210,11 +210,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
     const uint32_t a_off0 = (uint32_t)((32 * g + lane) * A_SBO + (r >> 1) * A_LBO + (4 * (r & 1)) * 16);
     const uint32_t a_off1 = a_off0 + (uint32_t)(64 * A_SBO);
 
-    long long it = a.cta_item[blockIdx.x];
-    const long long it_end = a.cta_item[blockIdx.x + 1];
-    if (it >= it_end) return;
-    int visit = a.cta_visit[blockIdx.x] - 1;
-    int region = -1;
+    int member;
+    const int pq = cta_pool(a, &member);
+    const Walk wk = pool_walk(a, pq);
+    if (tid == 0) {   // the CTA's first item
+        ts.q_tail = 0;
+        ts.q_done = 0;
+        long long s0;
+        (void)pool_take(a, pq, wk, ts, 0, &s0);
+    }
+    __syncthreads();
+    if (ts.q_tail == 0) return;   // the other CTA of the pool took every item
+    int head = 0;                 // this CTA's item number
+    long long step = ts.q_step[0];  // walk step of the current item
+    int visit = -1;
+    int run = a.pool_run[pq];     // run (one region along the pool's walk) of the current item
+    const int run_end = a.pool_run[pq + 1];
+    int open_run = -1;
 
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tm);
     if (warp == 0) tmem_alloc(tslot, TC_TCOLS);
@@ -240,12 +252,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
     tmem_fence_after();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(tslot);
 
-    ItemCtx cur = item_ctx(a, decode_item(a, it), TC_TB);
+    ItemCtx cur = item_ctx(a, decode_item(a, walk_item(wk, step)), TC_TB);
     if (tid == 0) {
         issue_stage(a, maps, cur, 0, smem, L, 0, 0);
         ItemCtx nx;
         int nch;
-        if (advance_chunk(a, it, 0, 1, it_end, TC_TB, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1, 1);
+        if (advance_chunk(a, pq, wk, ts, 0, 0, 1, TC_TB, &nx, &nch)) issue_stage(a, maps, nx, nch, smem, L, 1, 1);
     }
     unsigned gch = 0;       // chunk sequence number within this CTA
     unsigned kbs = 0;       // K-block sequence number within this CTA
@@ -253,10 +265,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
 
     while (true) {
         const ProbDev& P = a.probs[cur.q];
-        if (!a.dense && cur.region != region) {
-            if (region >= 0) topk_close_visit<TC_THREADS>(a, visit, ts, sm);
-            ++visit;
-            region = cur.region;
+        if (!a.dense) {   // new run of the pool's walk -> new visit buffer (this member's)
+            while (run + 1 < run_end && step >= a.run_step[run + 1]) ++run;
+            if (run != open_run) {
+                if (open_run >= 0) topk_close_visit<TC_THREADS>(a, visit, ts, sm);
+                visit = 2 * run + member;
+                open_run = run;
+            }
         }
         if (tid == 0) {
             const double sw = P.sum_w[cur.s], sw2 = P.sum_w2[cur.s];
@@ -417,9 +432,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
                 __threadfence_block();
                 const unsigned prev = atomicAdd(&done[buf], 1u);
                 if (prev == (unsigned)TC_PRODUCERS * ((gch >> 1) + 1) - 1) {
+                    __threadfence_block();   // the previous issuer's writes of the item ring
                     ItemCtx nx;
                     int nch;
-                    if (advance_chunk(a, it, ch, 2, it_end, TC_TB, &nx, &nch))
+                    if (advance_chunk(a, pq, wk, ts, head, ch, 2, TC_TB, &nx, &nch))
                         issue_stage(a, maps, nx, nch, smem, L, buf, (int)gch + 2);
                 }
             }
@@ -433,12 +449,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
         tc_emit(a, P, cur, tbase, visit, ts, sm);
         tmem_fence_before();
 
-        ++it;
-        if (it >= it_end) break;
-        cur = item_ctx(a, decode_item(a, it), TC_TB);
+        // the last chunk's issuer has taken the next item or found the pool exhausted
+        ++head;
+        if (head >= ts.q_tail) break;
+        step = ts.q_step[head & 3];
+        cur = item_ctx(a, decode_item(a, walk_item(wk, step)), TC_TB);
         __syncthreads();
     }
-    if (!ts.abort && !a.dense) topk_close_visit<TC_THREADS>(a, visit, ts, sm);
+    if (!ts.abort && !a.dense && open_run >= 0) topk_close_visit<TC_THREADS>(a, visit, ts, sm);
     if (ts.abort && tid == 0) {
         // copies and MMAs still in flight into this CTA's shared and tensor memory: wait for them
         const int* inflight = inflight_slots(smem, L);

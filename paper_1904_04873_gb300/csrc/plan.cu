@@ -178,11 +178,17 @@ struct bsh_plan {
     int skip_stage = -1;                   // test hook: stage left unissued in every CTA (-1: none)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
+    int pools = 0;                    // batched: CTAs c and c + pools share pool c
+    std::vector<int64_t> pool_item;   // [pools + 1] item range of each pool
+    std::vector<int32_t> pool_sweep;  // [2 * pools] walk rotation r and sweep length P
+    std::vector<int32_t> pool_run;    // [pools + 1] runs of each pool in run_step
+    std::vector<int64_t> run_step;    // [runs] first walk step of each run
     std::vector<int32_t> region_problem, region_visit_off, region_visits;
     // plain mode: per-region schedules
     std::vector<int32_t> pl_off, pl_ctas;
     // workspace layout
-    size_t off_probs = 0, off_cta_item = 0, off_cta_visit = 0, off_vbuf = 0, off_vcount = 0;
+    size_t off_probs = 0, off_cta_item = 0, off_cta_visit = 0, off_pool_item = 0, off_pool_sweep = 0,
+           off_pool_run = 0, off_run_step = 0, off_pool_next = 0, off_vbuf = 0, off_vcount = 0;
     size_t off_rprob = 0, off_rvoff = 0, off_rvis = 0, off_scratch = 0, off_dense = 0, ws_size = 0;
     unsigned char* ws = nullptr;
     bool bound = false;
@@ -219,17 +225,40 @@ std::vector<int> tune_chunks(const bsh_plan* p) {
 
 int build_schedule(bsh_plan* p, long long item_limit = -1);
 
-// f0 block and binary tile of item `loc` of a problem, in the batched kernel's item order:
-// patches in turn, inside a patch binary tiles, then sky points, then f0 blocks.
+// f0 block and binary tile of item `loc` of a problem, in the kernels' item order: sky
+// points in turn, inside a sky point binary tiles, then f0 blocks.
 void item_fb_bt(const ProbHost& h, long long loc, int* fb, int* bt) {
     const ProbDev& pd = h.pd;
     const long long per_s = (long long)pd.n_fb * pd.n_bt;
-    const int patch = h.patch_of_s[loc / per_s];
-    const long long p0 = h.ps[patch];
-    const long long per_bt = (h.ps[patch + 1] - p0) * pd.n_fb;
-    const long long off = loc - p0 * per_s;
-    *bt = (int)(off / per_bt);
-    *fb = (int)((off - (long long)*bt * per_bt) % pd.n_fb);
+    const int rem = (int)(loc % per_s);
+    *bt = rem / pd.n_fb;
+    *fb = rem % pd.n_fb;
+}
+
+// The contiguous item runs, in walk order, of a pool with range [a, a + len), sweep length P
+// and rotation r (the batched kernels' walk): sweep j starts at offset r of
+// [a + jP, a + (j+1)P) and wraps round; a last partial sweep of m <= r items (inside one sky
+// point, whose tiles P - r ... P - r + m - 1 it holds) starts at its tile that is a multiple
+// of m.
+template <class F>
+void walk_runs(long long a, long long len, long long P, long long r, F&& run) {
+    if (len <= 0) return;
+    if (r == 0) {
+        run(a, a + len);
+        return;
+    }
+    for (long long j0 = 0; j0 < len; j0 += P) {
+        const long long m = std::min(P, len - j0);
+        const long long e = std::max(m - r, 0LL);
+        if (e == 0 && m < P) {
+            const long long rho = (m - (P - r) % m) % m;
+            run(a + j0 + rho, a + j0 + m);
+            if (rho > 0) run(a + j0, a + j0 + rho);
+            continue;
+        }
+        if (e > 0) run(a + j0 + r, a + j0 + r + e);
+        if (m - e > 0) run(a + j0, a + j0 + (m - e));
+    }
 }
 int upload_plan(bsh_plan* p, cudaStream_t st);
 
@@ -604,21 +633,68 @@ int build_schedule(bsh_plan* p, long long item_limit) {
             p->cta_item[c] = std::min(it, total_items);
         }
         for (long long c = 1; c <= C; ++c) p->cta_item[c] = std::max(p->cta_item[c], p->cta_item[c - 1]);
-        p->cta_visit.assign(C + 1, 0);
-        int v = 0;
-        for (long long c = 0; c < C; ++c) {
-            p->cta_visit[c] = v;
-            const long long a = p->cta_item[c], b = p->cta_item[c + 1];
+        p->cta_visit.assign(C + 1, 0);   // (the plain kernel's)
+        // pools: CTAs c and c + H share pool c, the cost-balanced range of CTA slots 2c, 2c + 1
+        const long long H = (C + 1) / 2;
+        p->pools = (int)H;
+        p->pool_item.assign(H + 1, 0);
+        for (long long q = 0; q < H; ++q) p->pool_item[q] = p->cta_item[2 * q];
+        p->pool_item[H] = p->cta_item[C];
+        // the walk of each pool: a range inside one problem, with at most one region boundary
+        // inside, sweeps that problem's sky points from the first binary tile of its first whole
+        // sky point (see walk_runs); any other range is walked in order
+        p->pool_sweep.assign(2 * H, 0);
+        for (long long q = 0; q < H; ++q) {
+            const long long a = p->pool_item[q], b = p->pool_item[q + 1];
             if (a >= b) continue;
-            int r = (int)(std::upper_bound(r_begin.begin(), r_begin.end(), a) - r_begin.begin()) - 1;
-            while (r < p->regions && r_begin[r] < b) {
-                if (r_begin[r + 1] > r_begin[r] && r_begin[r + 1] > a) rvis[r].push_back(v++);
-                ++r;
-            }
+            int pi = 0;
+            while (pi + 1 < p->n && a >= p->P[pi + 1].pd.item_begin) ++pi;
+            const ProbDev& pd = p->P[pi].pd;
+            const long long P = (long long)pd.n_fb * pd.n_bt;
+            if (b > pd.item_begin + pd.n_items || P <= 0) continue;   // spans problems
+            const long long r = (P - (a - pd.item_begin) % P) % P;
+            if (r >= b - a) continue;                                  // no sky point boundary inside
+            int inner = 0;
+            long long prev = a;
+            for (auto it = std::upper_bound(r_begin.begin(), r_begin.end(), a); it != r_begin.end() && *it < b; ++it)
+                if (*it != prev) {
+                    ++inner;
+                    prev = *it;
+                }
+            if (inner > 1) continue;
+            p->pool_sweep[2 * q] = (int32_t)r;
+            p->pool_sweep[2 * q + 1] = (int32_t)P;
         }
-        p->cta_visit[C] = v;
-        p->visits = v;
-        p->visit_cap = (int)C + p->regions;   // bound for any split of the work list
+        // runs: the maximal stretches of one region along each pool's walk; run j owns visits 2j
+        // (the pool's first CTA) and 2j + 1 (its second)
+        p->pool_run.assign(H + 1, 0);
+        p->run_step.clear();
+        for (long long q = 0; q < H; ++q) {
+            p->pool_run[q] = (int32_t)p->run_step.size();
+            const bool pair = q + H < C;
+            int last = -1;
+            long long steps = 0;   // walk steps before the current stretch
+            walk_runs(p->pool_item[q], p->pool_item[q + 1] - p->pool_item[q], p->pool_sweep[2 * q + 1],
+                      p->pool_sweep[2 * q], [&](long long a, long long b) {
+                          int r = (int)(std::upper_bound(r_begin.begin(), r_begin.end(), a) - r_begin.begin()) - 1;
+                          while (r < p->regions && r_begin[r] < b) {
+                              if (r_begin[r + 1] > r_begin[r] && r_begin[r + 1] > a && r != last) {
+                                  const int j = (int)p->run_step.size();
+                                  p->run_step.push_back(steps + std::max(a, r_begin[r]) - a);
+                                  rvis[r].push_back(2 * j);
+                                  if (pair) rvis[r].push_back(2 * j + 1);
+                                  last = r;
+                              }
+                              ++r;
+                          }
+                          steps += b - a;
+                      });
+        }
+        p->pool_run[H] = (int32_t)p->run_step.size();
+        p->visits = 2 * (int)p->run_step.size();
+        // bound for any split of the work list: a contiguous range meets one run per region it
+        // meets; a rotated walk (at most one region boundary inside) adds at most two
+        p->visit_cap = 2 * ((int)H + p->regions + 2 * (int)std::min<long long>(H, p->regions));
     } else {
         // one launch per region, each with its own small persistent grid
         const long long Cmax = (long long)p->num_sms * cps;
@@ -641,6 +717,11 @@ int build_schedule(bsh_plan* p, long long item_limit) {
             p->cta_visit.push_back(v);
         }
         p->pl_off[p->regions] = (int)p->cta_item.size();
+        p->pools = 0;
+        p->pool_item.assign(1, 0);
+        p->pool_sweep.clear();
+        p->pool_run.assign(1, 0);
+        p->run_step.clear();
         p->visits = v;
         p->visit_cap = v;
         p->ctas = (int)Cmax;
@@ -672,6 +753,11 @@ int build_schedule(bsh_plan* p, long long item_limit) {
     }
     p->off_cta_item = o; o = al(o + sizeof(int64_t) * p->cta_item.size());
     p->off_cta_visit = o; o = al(o + sizeof(int32_t) * p->cta_visit.size());
+    p->off_pool_item = o; o = al(o + sizeof(int64_t) * p->pool_item.size());
+    p->off_pool_sweep = o; o = al(o + sizeof(int32_t) * std::max<size_t>(1, p->pool_sweep.size()));
+    p->off_pool_run = o; o = al(o + sizeof(int32_t) * p->pool_run.size());
+    p->off_run_step = o; o = al(o + sizeof(int64_t) * std::max<size_t>(1, p->run_step.size()));
+    p->off_pool_next = o; o = al(o + sizeof(unsigned long long) * std::max(1, p->pools));
     p->off_vbuf = o; o = al(o + sizeof(Entry) * (size_t)p->visit_cap * p->cap);
     p->off_vcount = o; o = al(o + sizeof(int32_t) * (size_t)std::max(1, p->visit_cap));
     p->off_rprob = o; o = al(o + sizeof(int32_t) * p->regions);
@@ -733,6 +819,12 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.n_probs = p->n;
     a.cta_item = reinterpret_cast<const int64_t*>(p->ws + p->off_cta_item);
     a.cta_visit = reinterpret_cast<const int32_t*>(p->ws + p->off_cta_visit);
+    a.pools = p->pools;
+    a.pool_item = reinterpret_cast<const int64_t*>(p->ws + p->off_pool_item);
+    a.pool_sweep = reinterpret_cast<const int32_t*>(p->ws + p->off_pool_sweep);
+    a.pool_run = reinterpret_cast<const int32_t*>(p->ws + p->off_pool_run);
+    a.run_step = reinterpret_cast<const int64_t*>(p->ws + p->off_run_step);
+    a.pool_next = reinterpret_cast<unsigned long long*>(p->ws + p->off_pool_next);
     a.visit_buf = reinterpret_cast<Entry*>(p->ws + p->off_vbuf);
     a.visit_count = reinterpret_cast<int32_t*>(p->ws + p->off_vcount);
     a.cap = p->cap;
@@ -765,6 +857,12 @@ int run_count(bsh_plan* p, int dense, cudaStream_t st) {
     for (int q = 0; q < p->n; ++q) launch_tables(p->P[q].pd, dprobs + q, p->mode, sp, st);
     CountArgs a = count_args(p, dense);
     if (p->mode == BSH_MODE_BATCHED) {
+        // every pool's item counter starts at 0; a visit buffer that neither CTA of its pool
+        // opens (the other took all of the run's items) holds no entries
+        cudaError_t e = cudaMemsetAsync(p->ws + p->off_pool_next, 0, sizeof(unsigned long long) * p->pools, st);
+        if (e == cudaSuccess && !dense && p->visits > 0)
+            e = cudaMemsetAsync(p->ws + p->off_vcount, 0, sizeof(int32_t) * p->visits, st);
+        if (e != cudaSuccess) return cuda_fail(e);
         if (p->acc_mode == 2) launch_count_tc(a, p->maps, p->ctas, st);
         else launch_count(a, p->maps, p->ctas, p->threads, st);
     } else {
@@ -833,6 +931,10 @@ int upload_plan(bsh_plan* p, cudaStream_t st) {
     cudaError_t e = up(p->ws + p->off_probs, hp.data(), hp.size(), st);
     e = e ? e : up(p->ws + p->off_cta_item, p->cta_item.data(), p->cta_item.size(), st);
     e = e ? e : up(p->ws + p->off_cta_visit, p->cta_visit.data(), p->cta_visit.size(), st);
+    e = e ? e : up(p->ws + p->off_pool_item, p->pool_item.data(), p->pool_item.size(), st);
+    e = e ? e : up(p->ws + p->off_pool_sweep, p->pool_sweep.data(), p->pool_sweep.size(), st);
+    e = e ? e : up(p->ws + p->off_pool_run, p->pool_run.data(), p->pool_run.size(), st);
+    e = e ? e : up(p->ws + p->off_run_step, p->run_step.data(), p->run_step.size(), st);
     e = e ? e : up(p->ws + p->off_rprob, p->region_problem.data(), p->region_problem.size(), st);
     e = e ? e : up(p->ws + p->off_rvoff, p->region_visit_off.data(), p->region_visit_off.size(), st);
     e = e ? e : up(p->ws + p->off_rvis, p->region_visits.data(), p->region_visits.size(), st);
