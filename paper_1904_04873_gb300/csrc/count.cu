@@ -76,7 +76,7 @@ __host__ __device__ inline Layout make_layout(int I, int wseg, int ot_max, int w
     L.done = o; o = align128(o + 16);
     L.tm = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
-    L.misc = o; o = align128(o + 64);
+    L.misc = o; o = align128(o + (int)sizeof(TopSmem));
     L.total = o;
     return L;
 }

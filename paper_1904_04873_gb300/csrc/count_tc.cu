@@ -70,7 +70,7 @@ __host__ __device__ inline TcLayout make_tc_layout(int I, int wseg, int ot_max, 
     L.done = o; o = align128(o + 16);
     L.tm = o; o = align128(o + 16);
     L.sel = o; o = align128(o + (int)sizeof(SelectSmem));
-    L.misc = o; o = align128(o + 64);
+    L.misc = o; o = align128(o + (int)sizeof(TopSmem));
     L.total = o;
     return L;
 }
