@@ -98,7 +98,8 @@ int bsh_sync_status(bsh_stream stream);
 /* median_window: odd width of the running median (the paper uses 101), or   */
 /*   0.  The noise floor is <n>^2 = median / ln 2 (median of Exp(1) is ln 2); */
 /*   near the band edges the window is shifted, not truncated, so K must be   */
-/*   >= median_window.                                                        */
+/*   >= median_window.  A row and its W words are staged in shared memory:   */
+/*   with a median, (K + W) * 4 bytes must not exceed 200 KB (BSH_ERR_ARG).  */
 /* rho_out [N][K] float (may be NULL): rho = P ln2 / median, rounded once    */
 /*   from double.                                                             */
 /* bits [N][W] uint32: bit (k & 31) of word k/32 of row i is 1 when          */

@@ -415,7 +415,7 @@ int bsh_make_peakgram(const float* power, int N, int K, int median_window, doubl
     if (N < 0 || K <= 0 || W < (K + 31) / 32 || !bits || (N > 0 && !power)) return BSH_ERR_ARG;
     if (median_window < 0 || (median_window > 0 && (median_window % 2 == 0 || median_window > K)))
         return BSH_ERR_ARG;
-    if (median_window > 0 && (size_t)K * sizeof(float) > 200 * 1024) return BSH_ERR_ARG;
+    if (median_window > 0 && ((size_t)K + (size_t)W) * sizeof(float) > 200 * 1024) return BSH_ERR_ARG;
     if (!std::isfinite(rho_th)) return BSH_ERR_ARG;
     launch_peakgram(power, N, K, median_window, rho_th, rho_out, bits, W, (cudaStream_t)stream);
     return cuda_fail(cudaGetLastError());

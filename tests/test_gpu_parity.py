@@ -55,6 +55,27 @@ def test_peakgram_direct_and_ragged(K):
         assert np.array_equal(rho.cpu().numpy(), orho)
 
 
+@pytest.mark.parametrize("window,K", [(3, 3), (7, 70), (31, 64), (101, 101), (101, 164), (101, 230),
+                                      (201, 2000), (63, 127)])
+@pytest.mark.parametrize("ties", [False, True])
+def test_peakgram_sliding_median(window, K, ties):
+    # the sliding running median (one segment of 63 bins per thread, the median moving to its
+    # successor or predecessor as the window slides) against the oracle's sort per bin: window
+    # sizes from 3 up, rows that end inside the first and second segments, and rows of small
+    # integers whose windows hold many equal values
+    rng = np.random.default_rng(1000 * window + K)
+    if ties:
+        r = rng.integers(0, 6, size=(41, K)).astype(np.float32) + 0.5
+    else:
+        r = (-np.log1p(-rng.random((41, K)))).astype(np.float32)
+    W = -(-(-(-K // 32)) // 4) * 4
+    rho, bits = bsh.make_peakgram(torch.as_tensor(r, device="cuda"), window, 1.6, W)
+    assert bsh.sync_status() == bsh.OK
+    orho, obits = oracle.peakgram(r, window, 1.6, W=W)
+    assert np.array_equal(bits.cpu().numpy().view(np.uint32), obits)
+    assert np.array_equal(rho.cpu().numpy(), orho)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("n_per_det", [300, 2500])
 def test_weights(dtype, n_per_det):
