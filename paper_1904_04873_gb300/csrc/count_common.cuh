@@ -105,12 +105,12 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
     return r;
 }
 
-// Work of the batched kernels.  CTAs c and c + pools (c < pools) share pool c: a contiguous,
-// cost-balanced range [base, base + len) of the item list, walked in a fixed order (below),
-// from which the two CTAs take one item at a time with an atomic counter.  Of the two CTAs
+// Work of the batched kernels.  CTAs c + m * pools (m < kPool, c < pools) share pool c: a
+// contiguous, cost-balanced range [base, base + len) of the item list, walked in a fixed order
+// (below), from which its CTAs take one item at a time with an atomic counter.  Of the two CTAs
 // resident on an SM, the warp schedulers favour one; with fixed ranges the favoured one
 // finishes early and the other runs on alone at a fraction of the SM's issue rate.  A pool
-// pairs an early CTA with a late one, and the pair ends together.
+// mixes early CTAs (low block indices) with late ones, and its CTAs end together.
 //
 // The walk covers the range in sweeps of P items (one sky point's binary tiles and f0
 // blocks).  Sweep j covers the items [base + jP, base + (j+1)P), started at offset r (the
@@ -127,11 +127,11 @@ struct Walk {
     long long r;
 };
 
-// Pool of this CTA and its member index (0 or 1) in the pool.
+// Pool of this CTA and its member index (0 ... kPool - 1) in the pool.
 __device__ __forceinline__ int cta_pool(const CountArgs& a, int* member) {
     const int c = (int)blockIdx.x;
-    *member = c >= a.pools ? 1 : 0;
-    return c >= a.pools ? c - a.pools : c;
+    *member = c / a.pools;
+    return c - *member * a.pools;
 }
 
 __device__ __forceinline__ Walk pool_walk(const CountArgs& a, int q) {

@@ -634,11 +634,17 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         }
         for (long long c = 1; c <= C; ++c) p->cta_item[c] = std::max(p->cta_item[c], p->cta_item[c - 1]);
         p->cta_visit.assign(C + 1, 0);   // (the plain kernel's)
-        // pools: CTAs c and c + H share pool c, the cost-balanced range of CTA slots 2c, 2c + 1
-        const long long H = (C + 1) / 2;
+        // pools: CTAs q + m H (m < kPool) share pool q, the cost-balanced range of as many
+        // consecutive CTA slots as it has CTAs
+        const long long H = (C + kPool - 1) / kPool;
         p->pools = (int)H;
+        auto members = [&](long long q) {
+            int n = 0;
+            for (int m = 0; m < kPool; ++m) n += q + m * H < C ? 1 : 0;
+            return n;
+        };
         p->pool_item.assign(H + 1, 0);
-        for (long long q = 0; q < H; ++q) p->pool_item[q] = p->cta_item[2 * q];
+        for (long long q = 0, slot = 0; q < H; slot += members(q), ++q) p->pool_item[q] = p->cta_item[slot];
         p->pool_item[H] = p->cta_item[C];
         // the walk of each pool: a range inside one problem, with at most one region boundary
         // inside, sweeps that problem's sky points from the first binary tile of its first whole
@@ -665,13 +671,13 @@ int build_schedule(bsh_plan* p, long long item_limit) {
             p->pool_sweep[2 * q] = (int32_t)r;
             p->pool_sweep[2 * q + 1] = (int32_t)P;
         }
-        // runs: the maximal stretches of one region along each pool's walk; run j owns visits 2j
-        // (the pool's first CTA) and 2j + 1 (its second)
+        // runs: the maximal stretches of one region along each pool's walk; run j owns visits
+        // kPool j + m, one for each CTA m of the pool
         p->pool_run.assign(H + 1, 0);
         p->run_step.clear();
         for (long long q = 0; q < H; ++q) {
             p->pool_run[q] = (int32_t)p->run_step.size();
-            const bool pair = q + H < C;
+            const int nm = members(q);
             int last = -1;
             long long steps = 0;   // walk steps before the current stretch
             walk_runs(p->pool_item[q], p->pool_item[q + 1] - p->pool_item[q], p->pool_sweep[2 * q + 1],
@@ -681,8 +687,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
                               if (r_begin[r + 1] > r_begin[r] && r_begin[r + 1] > a && r != last) {
                                   const int j = (int)p->run_step.size();
                                   p->run_step.push_back(steps + std::max(a, r_begin[r]) - a);
-                                  rvis[r].push_back(2 * j);
-                                  if (pair) rvis[r].push_back(2 * j + 1);
+                                  for (int m = 0; m < nm; ++m) rvis[r].push_back(kPool * j + m);
                                   last = r;
                               }
                               ++r;
@@ -691,10 +696,10 @@ int build_schedule(bsh_plan* p, long long item_limit) {
                       });
         }
         p->pool_run[H] = (int32_t)p->run_step.size();
-        p->visits = 2 * (int)p->run_step.size();
+        p->visits = kPool * (int)p->run_step.size();
         // bound for any split of the work list: a contiguous range meets one run per region it
         // meets; a rotated walk (at most one region boundary inside) adds at most two
-        p->visit_cap = 2 * ((int)H + p->regions + 2 * (int)std::min<long long>(H, p->regions));
+        p->visit_cap = kPool * ((int)H + p->regions + 2 * (int)std::min<long long>(H, p->regions));
     } else {
         // one launch per region, each with its own small persistent grid
         const long long Cmax = (long long)p->num_sms * cps;

@@ -1,14 +1,14 @@
 """The batched kernels' pooled walk over the item list, against the FP64 oracle.
 
-Items are ordered sky point, binary tile, f0 block.  CTAs c and c + C/2 share a pool: a
-contiguous range of items that the two take one at a time, in the pool's walk order.  A pool
+Items are ordered sky point, binary tile, f0 block.  CTAs c + m C/4 (m < 4) share a pool: a
+contiguous range of items that they take one at a time, in the pool's walk order.  A pool
 holding more than one sky point's items (P of them) walks them in sweeps of P, each started at
 the first binary tile of the next sky point and wrapped round.  These problems have few items
 per sky point and many sky points, so most pools walk rotated sweeps: every item must still be
 counted exactly once (dense counts), a range that holds a sky-patch boundary meets the two
 patches in turn (up to four runs, each with one toplist visit per CTA of the pool), and the
 visits must merge to the oracle's per-patch toplists, the same on every launch however the
-two CTAs split the items.
+pool's CTAs split the items.
 """
 import math
 
@@ -35,7 +35,7 @@ def built():
 
 def _sky_many(patch_size):
     # 400 sky points, 64 SFTs, 8 binaries (one tile), 90 f0 templates (3 blocks of 30):
-    # P = 3 items per sky point, 1200 items over at most 304 CTAs (152 pools)
+    # P = 3 items per sky point, 1200 items over at most 304 CTAs (76 pools)
     return small_mid(n_sky=400, n_per_det=32, n_ap=2, n_P=2, n_T=2, patch_size=patch_size, top_k=20)
 
 
@@ -83,8 +83,8 @@ def test_toplists_merge_over_revisited_patches(many_sky, acc):
 
 
 def test_pooled_ctas_give_the_same_toplists_every_launch(many_sky):
-    # the two CTAs of a pool split its items differently from launch to launch (whichever
-    # takes the next item first); the toplists (sorted by score, then template id) must not
+    # the CTAs of a pool split its items differently from launch to launch (whichever takes
+    # the next item first); the toplists (sorted by score, then template id) must not
     pr, dp, _, _ = many_sky
     plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k, threads=256)
     first = None
