@@ -353,21 +353,22 @@ inline void ensure_smem(K kernel, int bytes, int* done) {
 }
 
 // ---------------------------------------------------------------- launches
-// CTAs per item pool of the batched kernels: two SMs' worth, each SM holding one CTA that its
-// warp schedulers favour and one that they do not
-constexpr int kPool = 4;
+// CTAs per item pool of the batched kernels at most: two SMs' worth, each SM holding one CTA
+// that its warp schedulers favour and one that they do not
+constexpr int kPoolMax = 4;
 
 struct CountArgs {
     const ProbDev* probs;        // device array [n_probs]
     int n_probs;
     const int64_t* cta_item;     // [ctas + 1] item range per CTA (plain kernel)
     const int32_t* cta_visit;    // [ctas] first visit index per CTA (plain kernel)
-    // batched kernels: CTAs c + m * pools (m < kPool) share pool c (c < pools)
+    // batched kernels: CTAs c + m * pools (m < pool_size) share pool c (c < pools)
     int pools;
+    int pool_size;               // CTAs per pool (2 or kPoolMax)
     const int64_t* pool_item;    // [pools + 1] item range of each pool
     const int32_t* pool_sweep;   // [2 * pools] walk of each pool: rotation r, sweep length P
     const int32_t* pool_run;     // [pools + 1] each pool's runs (one region along its walk) in run_step
-    const int64_t* run_step;     // [runs] first walk step of each run; run j owns visits kPool j + m
+    const int64_t* run_step;     // [runs] first walk step of each run; run j owns visits pool_size j + m
     unsigned long long* pool_next;  // [pools] next walk step of each pool (zeroed before each launch)
     Entry* visit_buf;            // [visits][cap]
     int32_t* visit_count;        // [visits]

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS)
             while (run + 1 < run_end && step >= a.run_step[run + 1]) ++run;
             if (run != open_run) {
                 if (open_run >= 0) topk_close_visit<THREADS>(a, visit, ts, sm);
-                visit = kPool * run + member;
+                visit = a.pool_size * run + member;
                 open_run = run;
             }
         }

@@ -105,7 +105,7 @@ __device__ __forceinline__ Item decode_item(const CountArgs& a, long long it) {
     return r;
 }
 
-// Work of the batched kernels.  CTAs c + m * pools (m < kPool, c < pools) share pool c: a
+// Work of the batched kernels.  CTAs c + m * pools (m < pool_size, c < pools) share pool c: a
 // contiguous, cost-balanced range [base, base + len) of the item list, walked in a fixed order
 // (below), from which its CTAs take one item at a time with an atomic counter.  Of the two CTAs
 // resident on an SM, the warp schedulers favour one; with fixed ranges the favoured one
@@ -127,7 +127,7 @@ struct Walk {
     long long r;
 };
 
-// Pool of this CTA and its member index (0 ... kPool - 1) in the pool.
+// Pool of this CTA and its member index (0 ... pool_size - 1) in the pool.
 __device__ __forceinline__ int cta_pool(const CountArgs& a, int* member) {
     const int c = (int)blockIdx.x;
     *member = c / a.pools;

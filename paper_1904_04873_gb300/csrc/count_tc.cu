@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) count_tc(const CountArgs a, con
             while (run + 1 < run_end && step >= a.run_step[run + 1]) ++run;
             if (run != open_run) {
                 if (open_run >= 0) topk_close_visit<TC_THREADS>(a, visit, ts, sm);
-                visit = kPool * run + member;
+                visit = a.pool_size * run + member;
                 open_run = run;
             }
         }

@@ -178,7 +178,8 @@ struct bsh_plan {
     int skip_stage = -1;                   // test hook: stage left unissued in every CTA (-1: none)
     std::vector<int64_t> cta_item;
     std::vector<int32_t> cta_visit;
-    int pools = 0;                    // batched: CTAs c and c + pools share pool c
+    int pools = 0;                    // batched: CTAs c + m * pools share pool c
+    int pool_size = 0;                // CTAs per pool
     std::vector<int64_t> pool_item;   // [pools + 1] item range of each pool
     std::vector<int32_t> pool_sweep;  // [2 * pools] walk rotation r and sweep length P
     std::vector<int32_t> pool_run;    // [pools + 1] runs of each pool in run_step
@@ -634,13 +635,20 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         }
         for (long long c = 1; c <= C; ++c) p->cta_item[c] = std::max(p->cta_item[c], p->cta_item[c - 1]);
         p->cta_visit.assign(C + 1, 0);   // (the plain kernel's)
-        // pools: CTAs q + m H (m < kPool) share pool q, the cost-balanced range of as many
-        // consecutive CTA slots as it has CTAs
-        const long long H = (C + kPool - 1) / kPool;
+        // pools: CTAs q + m H (m < G) share pool q, the cost-balanced range of as many
+        // consecutive CTA slots as it has CTAs.  Pools of four balance best, but a pool's range
+        // then spans twice the binary tiles of a pair's and the pools drift further apart in
+        // tiles; a fixed-point orbit table larger than half the L2 pays for that in DRAM
+        // re-reads (3.5x the bytes on the metric bank), so such plans use pairs.
+        size_t table = 0;
+        for (const auto& h : p->P) table = std::max(table, (size_t)h.pd.nOT * (size_t)h.pd.Np * sizeof(int32_t));
+        const int G = table > ((size_t)64 << 20) ? 2 : kPoolMax;
+        p->pool_size = G;
+        const long long H = (C + G - 1) / G;
         p->pools = (int)H;
         auto members = [&](long long q) {
             int n = 0;
-            for (int m = 0; m < kPool; ++m) n += q + m * H < C ? 1 : 0;
+            for (int m = 0; m < G; ++m) n += q + m * H < C ? 1 : 0;
             return n;
         };
         p->pool_item.assign(H + 1, 0);
@@ -672,7 +680,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
             p->pool_sweep[2 * q + 1] = (int32_t)P;
         }
         // runs: the maximal stretches of one region along each pool's walk; run j owns visits
-        // kPool j + m, one for each CTA m of the pool
+        // G j + m, one for each CTA m of the pool
         p->pool_run.assign(H + 1, 0);
         p->run_step.clear();
         for (long long q = 0; q < H; ++q) {
@@ -687,7 +695,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
                               if (r_begin[r + 1] > r_begin[r] && r_begin[r + 1] > a && r != last) {
                                   const int j = (int)p->run_step.size();
                                   p->run_step.push_back(steps + std::max(a, r_begin[r]) - a);
-                                  for (int m = 0; m < nm; ++m) rvis[r].push_back(kPool * j + m);
+                                  for (int m = 0; m < nm; ++m) rvis[r].push_back(G * j + m);
                                   last = r;
                               }
                               ++r;
@@ -696,10 +704,10 @@ int build_schedule(bsh_plan* p, long long item_limit) {
                       });
         }
         p->pool_run[H] = (int32_t)p->run_step.size();
-        p->visits = kPool * (int)p->run_step.size();
+        p->visits = G * (int)p->run_step.size();
         // bound for any split of the work list: a contiguous range meets one run per region it
         // meets; a rotated walk (at most one region boundary inside) adds at most two
-        p->visit_cap = kPool * ((int)H + p->regions + 2 * (int)std::min<long long>(H, p->regions));
+        p->visit_cap = G * ((int)H + p->regions + 2 * (int)std::min<long long>(H, p->regions));
     } else {
         // one launch per region, each with its own small persistent grid
         const long long Cmax = (long long)p->num_sms * cps;
@@ -723,6 +731,7 @@ int build_schedule(bsh_plan* p, long long item_limit) {
         }
         p->pl_off[p->regions] = (int)p->cta_item.size();
         p->pools = 0;
+        p->pool_size = 0;
         p->pool_item.assign(1, 0);
         p->pool_sweep.clear();
         p->pool_run.assign(1, 0);
@@ -825,6 +834,7 @@ CountArgs count_args(bsh_plan* p, int dense) {
     a.cta_item = reinterpret_cast<const int64_t*>(p->ws + p->off_cta_item);
     a.cta_visit = reinterpret_cast<const int32_t*>(p->ws + p->off_cta_visit);
     a.pools = p->pools;
+    a.pool_size = p->pool_size;
     a.pool_item = reinterpret_cast<const int64_t*>(p->ws + p->off_pool_item);
     a.pool_sweep = reinterpret_cast<const int32_t*>(p->ws + p->off_pool_sweep);
     a.pool_run = reinterpret_cast<const int32_t*>(p->ws + p->off_pool_run);
