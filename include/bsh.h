@@ -193,7 +193,9 @@ typedef struct bsh_count_options {
 typedef struct bsh_plan bsh_plan;
 
 /* Validates the problems on the host, picks the fixed-point scales and the
- * static persistent schedule.  HOST only, no CUDA call.  patch_start and the
+ * persistent schedule: static cost-balanced ranges of the item list, each
+ * shared by a pool of CTAs (four, or two for orbit tables larger than half the
+ * L2) that take its items one at a time.  HOST only, no CUDA call.  patch_start and the
  * grid or bank arrays are copied; device pointers are stored and used by later
  * calls.
  * Returns BSH_ERR_RANGE when the band does not cover every track, when a
