@@ -376,6 +376,23 @@ int bsh_debug_track_windows(const bsh_problem* host_problem, const int32_t* quer
                             int count, const uint32_t* row_bits, uint32_t* out, int32_t* path);
 
 /* ------------------------------------------------------------------------ */
+/* Host-side view of the batched schedule (no GPU needed; no counterpart in  */
+/* the paper: the order of work is this library's).  The batched kernels'   */
+/* CTAs share the item list in pools: pool q is a contiguous, cost-balanced  */
+/* range of items that its CTAs (pool_size of them) take one at a time, in   */
+/* the pool's walk order.  Items of a problem run sky point, binary tile,    */
+/* f0 block (fastest); indices count from the first problem's first item.    */
+/* *n_pools and *pool_size receive the plan's counts (either may be NULL);   */
+/* for 0 <= pool < n_pools, *n_items (may be NULL) receives the pool's item  */
+/* count and, when items is not NULL and cap >= that count, items[] its walk */
+/* order.  BATCHED and LUT plans only (BSH_ERR_STATE otherwise); pool out of */
+/* range or cap too small: BSH_ERR_ARG.  The schedule is the one that        */
+/* bsh_plan_create, or the last bsh_autotune, left.                          */
+/* ------------------------------------------------------------------------ */
+int bsh_debug_pool_walk(const bsh_plan* plan, int pool, int64_t* items, int64_t cap, int64_t* n_items,
+                        int* n_pools, int* pool_size);
+
+/* ------------------------------------------------------------------------ */
 /* (vi) Post-processing, Sec. V.E: candidate parameters, the distance of      */
 /* Eq. (44), coincidences between two lists (option A), clustering, the       */
 /* option-B cut, significance-weighted centroids and each band's most         */

@@ -133,6 +133,8 @@ _SIGS = {
     "bsh_plan_set_direct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bsh_plan_direct": (ctypes.c_int, [ctypes.c_void_p]),
     "bsh_plan_set_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "bsh_debug_pool_walk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "bsh_cand_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
@@ -466,6 +468,23 @@ def debug_track_windows(pr, queries: np.ndarray, rows: np.ndarray):
     _check(lib().bsh_debug_track_windows(ctypes.byref(d), q.ctypes.data, n, rows.ctypes.data, out.ctypes.data,
                                          path.ctypes.data), "bsh_debug_track_windows")
     return out, path
+
+
+def debug_pool_walk(plan_handle, pool: int = -1):
+    """The batched schedule of a plan (a handle from bsh_plan_create): (number of pools, CTAs
+    per pool, pool `pool`'s item indices in walk order, or None for pool -1).  No GPU needed."""
+    npools, psize, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    rc = lib().bsh_debug_pool_walk(plan_handle, max(pool, 0), None, 0, ctypes.byref(n), ctypes.byref(npools),
+                                   ctypes.byref(psize))
+    if pool < 0:
+        if rc not in (OK, ERR_ARG):
+            _check(rc, "bsh_debug_pool_walk")
+        return npools.value, psize.value, None
+    _check(rc, "bsh_debug_pool_walk")
+    items = np.zeros(max(n.value, 1), np.int64)
+    _check(lib().bsh_debug_pool_walk(plan_handle, pool, items.ctypes.data, items.size, ctypes.byref(n), None, None),
+           "bsh_debug_pool_walk")
+    return npools.value, psize.value, items[:n.value]
 
 
 def binary_resolution(f, T_c, T_obs, a_p, Omega, m_a, m_Om, m_t):

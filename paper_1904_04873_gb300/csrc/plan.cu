@@ -516,6 +516,24 @@ void bsh_plan_destroy(bsh_plan* p) {
 }
 
 size_t bsh_plan_workspace_size(const bsh_plan* p) { return p ? p->ws_cap : 0; }
+
+int bsh_debug_pool_walk(const bsh_plan* p, int pool, int64_t* items, int64_t cap, int64_t* n_items, int* n_pools,
+                        int* pool_size) {
+    if (!p) return BSH_ERR_ARG;
+    if (p->mode != BSH_MODE_BATCHED) return BSH_ERR_STATE;
+    if (n_pools) *n_pools = p->pools;
+    if (pool_size) *pool_size = p->pool_size;
+    if (pool < 0 || pool >= p->pools) return BSH_ERR_ARG;
+    const long long a = p->pool_item[pool], len = p->pool_item[pool + 1] - a;
+    if (n_items) *n_items = len;
+    if (!items) return BSH_OK;
+    if (cap < len) return BSH_ERR_ARG;
+    long long k = 0;
+    walk_runs(a, len, p->pool_sweep[2 * pool + 1], p->pool_sweep[2 * pool], [&](long long x, long long y) {
+        for (long long i = x; i < y; ++i) items[k++] = i;
+    });
+    return BSH_OK;
+}
 int bsh_plan_num_regions(const bsh_plan* p) { return p ? p->regions : 0; }
 int bsh_plan_first_region(const bsh_plan* p, int q) {
     if (!p || q < 0 || q >= p->n) return -1;
