@@ -10,14 +10,15 @@ patches in turn (up to four runs, each with one toplist visit per CTA of the poo
 visits must merge to the oracle's per-patch toplists, the same on every launch however the
 pool's CTAs split the items.
 """
+import dataclasses
 import math
 
 import numpy as np
 import pytest
 
-from _common import small_mid
+from _common import oracle_dense_parallel, small_mid
 from gpu_common import check_dense, check_toplists, device_problem, oracle_scores
-from paper_1904_04873_gb300 import bsh
+from paper_1904_04873_gb300 import bsh, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -99,4 +100,26 @@ def test_pooled_ctas_give_the_same_toplists_every_launch(many_sky):
             continue
         for (ia, sa), (ib, sb) in zip(first, got):
             assert np.array_equal(ia, ib) and np.array_equal(sa, sb)
+    plan.close()
+
+
+def test_pairs_for_a_large_orbit_table_count_every_item_once():
+    # 4 200 orbit rows (70 Omega x 60 t_asc, one a_p) over 2 x 2 048 SFTs: a 69 MB fixed-point
+    # orbit table, more than half the L2, so the plan pools its CTAs in pairs (visits 2j + m);
+    # two sky points in patches of one, 32 f0 templates: 1.1e9 terms for the oracle
+    pr = synth.mid(n_sky=2, n_per_det=2048, n_ap=1, n_P=70, n_T=60, patch_size=1, top_k=20)
+    pr = dataclasses.replace(pr, n_f0=32)
+    dp, op, wq = device_problem(pr, "f16")
+    plan = bsh.Plan([dp], bsh.MODE_BATCHED, top_k=pr.top_k)
+    assert bsh.debug_pool_walk(plan.h)[1] == 2
+    gu, gw = plan.count_dense()
+    assert bsh.sync_status() == bsh.OK
+    d = oracle_dense_parallel(pr, op.bits, wq, [0, 1])
+    check_dense(gu[0], gw[0], d)
+    plan.number_count()
+    assert bsh.sync_status() == bsh.OK
+    p = math.exp(-pr.rho_th)
+    sw, sw2 = wq.sum(axis=1), (wq * wq).sum(axis=1)
+    sc = (d["n_w"] - p * sw[:, None, None]) / np.sqrt(p * (1 - p) * sw2)[:, None, None]
+    check_toplists(plan, dp, 0, [sc[0:1], sc[1:2]], pr.top_k, tol=2e-4)
     plan.close()
